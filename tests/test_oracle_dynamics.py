@@ -1,0 +1,109 @@
+"""Oracle pins: the neuron and synapse dynamics (Eq. 1-3 with exact integration).
+
+Each test checks the oracle against something other than its own propagator formula: the
+analytic post-synaptic potential, an independent ODE solver (scipy), step halving, and the
+analytic inter-spike interval under a constant current with the refractory clamp of Eq. 2."""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+from oracle import oracle as o
+
+TAU_M, TAU_S, C_M = 10.0, 0.5, 250.0
+
+
+def _single(prec=o.FP64, **kw):
+    p = o.Params(n_exc=1, n_inh=0, k_exc=0, k_inh=0, poisson_on=0, v_th=1e9, precision=prec, **kw)
+    net = o.Network(p, 1, edges=(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0)))
+    return p, net
+
+
+def test_psp_matches_analytic_curve():
+    """One input spike of weight J: V(t) = J/C tau_m tau_s/(tau_s - tau_m) (e^{-t/tau_s} - e^{-t/tau_m})."""
+    J, d, s0 = 87.8, 3, 5
+    p = o.Params(n_exc=2, n_inh=0, k_exc=0, k_inh=0, poisson_on=0, v_th=1e9, precision=o.FP64)
+    net = o.Network(p, 1, edges=([0], [1], [d], [J]))
+    net.set_state([0.0, 0.0], [0.0, 0.0], [0, 0])
+    n = 400
+    tr = net.simulate(n, forced=([s0], [0]), trace_ids=[1])[:, 0]
+    arrive = s0 + d                 # the input is added to I at the end of this step
+    assert np.all(tr[: arrive + 1] == 0.0)
+    m = np.arange(1, n - arrive)
+    t = m * p.dt
+    psp = J / C_M * TAU_M * TAU_S / (TAU_S - TAU_M) * (np.exp(-t / TAU_S) - np.exp(-t / TAU_M))
+    got = tr[arrive + 1:]
+    assert np.allclose(got, psp, rtol=1e-11, atol=1e-15)
+    # peak of the PSP: 0.14999 mV at t* = tau_m tau_s/(tau_m - tau_s) ln(tau_m/tau_s) = 1.5767 ms
+    t_star = TAU_M * TAU_S / (TAU_M - TAU_S) * math.log(TAU_M / TAU_S)
+    assert abs(t_star - 1.5767) < 1e-4
+    k = int(np.argmax(got))
+    assert abs(t[k] - t_star) <= p.dt
+    assert abs(got.max() - 0.14999) < 2e-5
+
+
+@pytest.mark.parametrize("v0,i0,ie", [(5.0, 300.0, 0.0), (-2.0, -150.0, 40.0), (12.0, 0.0, 0.0)])
+def test_free_evolution_matches_ode_solver(v0, i0, ie):
+    """dV/dt = -V/tau_m + (I + I_e)/C, dI/dt = -I/tau_s integrated by scipy (DOP853)."""
+    p, net = _single(i_e=ie)
+    net.set_state([v0], [i0], [0])
+    n = 300
+    tr = net.simulate(n, trace_ids=[0])[:, 0]
+    t_eval = (np.arange(n) + 1) * p.dt
+
+    def rhs(_, y):
+        return [-y[0] / TAU_M + (y[1] + ie) / C_M, -y[1] / TAU_S]
+
+    sol = solve_ivp(rhs, (0.0, t_eval[-1]), [v0, i0], method="DOP853", t_eval=t_eval, rtol=1e-12, atol=1e-13)
+    assert np.allclose(tr, sol.y[0], rtol=1e-9, atol=1e-10)
+    _, cur, _ = net.state()
+    assert np.isclose(cur[0], i0 * math.exp(-t_eval[-1] / TAU_S), rtol=1e-12, atol=1e-300)
+
+
+def test_step_halving_agrees_at_common_times():
+    """Exact integration is step-size independent: dt and dt/2 agree at shared grid times."""
+    traces = []
+    for dt, n in ((0.1, 200), (0.05, 400)):
+        p, net = _single(i_e=90.0, dt=dt)
+        net.set_state([3.0], [200.0], [0])
+        traces.append(net.simulate(n, trace_ids=[0])[:, 0])
+    assert np.allclose(traces[0], traces[1][1::2], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec", [o.FP64, o.FP32])
+def test_constant_current_interspike_interval(prec):
+    """Constant I_e: mu = tau_m I_e / C; first crossing T* = tau_m ln(mu / (mu - theta)).
+    Spikes at the first grid step whose end time reaches T*; then V is clamped to V_reset for
+    n_ref = 20 steps (Eq. 2) and the next crossing takes ceil(T*/dt) steps again."""
+    ie = 600.0
+    p = o.Params(n_exc=1, n_inh=0, k_exc=0, k_inh=0, poisson_on=0, i_e=ie, precision=prec)
+    net = o.Network(p, 1, edges=(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0)))
+    net.set_state([0.0], [0.0], [0])
+    n = 1000
+    tr = net.simulate(n, trace_ids=[0])[:, 0]
+    steps, ids = net.raster()
+    mu = TAU_M * ie / C_M
+    t_star = TAU_M * math.log(mu / (mu - p.v_th))
+    first = math.ceil(t_star / p.dt) - 1
+    isi = 20 + math.ceil(t_star / p.dt)
+    expect = np.arange(first, n, isi)
+    assert list(steps) == list(expect)
+    assert set(ids) == {0}
+    # refractory clamp: V == V_reset on the spike step and for exactly n_ref steps after it
+    s = int(steps[0])
+    assert np.all(tr[s: s + 21] == 0.0)
+    assert tr[s + 21] > 0.0
+
+
+def test_refractory_counter_and_current_keep_evolving():
+    """During the refractory period V stays at V_reset while I keeps decaying and receiving input."""
+    p = o.Params(n_exc=2, n_inh=0, k_exc=0, k_inh=0, poisson_on=0, v_th=1e9, precision=o.FP64)
+    net = o.Network(p, 1, edges=([0], [1], [1], [50.0]))
+    net.set_state([0.0, 0.0], [0.0, 100.0], [0, 5])
+    net.simulate(3, forced=([0], [0]))
+    v, cur, r = net.state()
+    assert v[1] == 0.0 and r[1] == 2
+    p11 = math.exp(-p.dt / TAU_S)
+    # step 0: I = P11*100; step 1: I = P11*I + 50 (spike from step 0, delay 1); step 2: decay
+    assert np.isclose(cur[1], ((100.0 * p11) * p11 + 50.0) * p11, rtol=1e-14)
