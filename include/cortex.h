@@ -1,0 +1,181 @@
+/*
+ * cortex.h -- C ABI of the GB300 spike-delivery library (CORTEX, arXiv 2406.03762).
+ *
+ * The library simulates spiking networks of leaky integrate-and-fire neurons (Eq. 1) with
+ * threshold, reset and refractory period (Eq. 2) and an exponentially decaying synaptic current
+ * (Eq. 3, read as a current-based synapse: an arriving spike adds its weight to the current).
+ * Connectivity is a fixed in-degree random graph G = (V, E) (Sec. II-A, Eq. 4).  Each thread
+ * block owns a contiguous range of post-synaptic neurons together with all of their incoming
+ * synapses -- the indegree sub-graph inS(V_i) of Eq. 5 and Eq. 9-10 -- so delivery into a
+ * neuron's delay ring buffer needs no atomics (Eq. 14, Sec. III-B "Avoid Data Racing").
+ * One simulation step follows Sec. II-B: spikes act on their targets after the synaptic delay,
+ * then every neuron updates and produces the next spikes.
+ *
+ * Conventions
+ *   - Every call returns CORTEX_OK (0) or a negative CORTEX_ERR_* code; no exception, abort or
+ *     exit crosses the ABI.  cortex_last_error() describes the most recent failure of the
+ *     calling thread.
+ *   - All device memory is allocated and owned by the library inside the cortex_net handle and
+ *     released by cortex_free().  Host buffers passed in are owned by the caller; the library
+ *     never keeps a pointer to them after the call returns.
+ *   - Work is issued on the CUDA stream passed at build time (a cudaStream_t given as void*;
+ *     NULL is the legacy default stream).  Calls on one handle must not overlap; calls that
+ *     return data to the host synchronise that stream.
+ *   - Time is counted in steps of dt.  Delays are integers d_min..d_max steps (d_min >= 1).
+ */
+#ifndef CORTEX_H
+#define CORTEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CORTEX_OK 0
+#define CORTEX_ERR_ARG (-1)          /* invalid argument or size; nothing was changed */
+#define CORTEX_ERR_OOM (-2)          /* device or host allocation failed */
+#define CORTEX_ERR_CUDA (-3)         /* a CUDA runtime call failed (see cortex_last_error) */
+#define CORTEX_ERR_TIMEOUT (-4)      /* a device-side wait gave up; the handle stays usable */
+#define CORTEX_ERR_UNSUPPORTED (-5)  /* sizes outside the supported range, or no capable GPU */
+#define CORTEX_ERR_OVERFLOW (-6)     /* an output buffer was too small (needed size returned) */
+
+/* synaptic weight storage */
+#define CORTEX_F32 0                 /* float weights (7 bytes per synapse with target, delay) */
+#define CORTEX_BF16 1                /* bfloat16 weights, round-to-nearest-even (5 bytes) */
+
+/* ring-buffer placement (cortex_options.ring) */
+#define CORTEX_RING_AUTO 0
+#define CORTEX_RING_SMEM 1           /* each block keeps its targets' ring in shared memory */
+#define CORTEX_RING_GLOBAL 2         /* the ring stays in global memory (owner-exclusive) */
+
+/* step-loop modes (cortex_options.mode) */
+#define CORTEX_MODE_PERSISTENT 0     /* one cooperative kernel per chunk, grid barrier inside */
+#define CORTEX_MODE_SPLIT 1          /* an update kernel and a delivery kernel per window */
+
+/* One network.  Units: ms, pF, mV, pA, Hz.  Neurons 0..n_exc-1 are excitatory, the rest
+ * inhibitory.  Each neuron receives exactly k_exc excitatory and k_inh inhibitory synapses,
+ * drawn with replacement (multapses and autapses allowed, Sec. II-A "x != y can be ignored").
+ * Weights: j_exc for excitatory sources, j_inh for inhibitory ones; external drive: a Poisson
+ * process of rate nu_ext_hz per neuron, each event adding j_ext to the synaptic current. */
+typedef struct cortex_params {
+  int32_t n_exc, n_inh, k_exc, k_inh;
+  float tau_m, c_m, tau_syn, v_th, v_reset, e_l, t_ref, dt;
+  float j_exc, j_inh;
+  int32_t d_min, d_max;
+  float nu_ext_hz, j_ext;
+  int32_t weight_dtype;              /* CORTEX_F32 or CORTEX_BF16 */
+} cortex_params;
+
+/* Tuning overrides; zero-initialise for automatic choices. */
+typedef struct cortex_options {
+  int32_t ring;                      /* CORTEX_RING_* */
+  int32_t mode;                      /* CORTEX_MODE_* */
+  int32_t warps_per_block;           /* 0 = auto; 1..14 */
+  int32_t targets_per_block;         /* 0 = auto; upper bound on targets owned by one block */
+  int32_t steps_per_launch;          /* 0 = auto; steps per persistent launch (graph node) */
+  int32_t use_graph;                 /* 0 = auto (on), 1 = on, -1 = off */
+  int64_t raster_capacity;           /* 0 = auto; spikes kept on the device per network */
+  double barrier_timeout_ms;         /* 0 = 2000 ms; device waits give up after this */
+} cortex_options;
+
+typedef struct cortex_stats_t {
+  int64_t n_nets;
+  int64_t n_neurons;                 /* over all networks */
+  int64_t n_synapses;                /* over all networks */
+  int64_t step;                      /* steps simulated so far */
+  int64_t spikes;                    /* spikes emitted so far, all networks */
+  int64_t events;                    /* synaptic events: sum over spikes of the out-degree */
+  double build_ms;                   /* device time of the last build */
+  double simulate_ms;                /* device time of the last cortex_simulate call */
+  int64_t simulate_steps;            /* steps of the last cortex_simulate call */
+  int64_t simulate_events;           /* events delivered during the last cortex_simulate */
+  int32_t n_blocks;                  /* thread blocks (indegree sub-graphs) of the step kernel */
+  int32_t threads_per_block;
+  int32_t ring_in_smem;              /* 1 if the ring lives in shared memory */
+  int32_t mode;                      /* CORTEX_MODE_* in use */
+  int64_t device_bytes;              /* device memory held by the handle */
+} cortex_stats_t;
+
+typedef struct cortex_net cortex_net;
+
+/* Build one network on the device from its parameters and a 64-bit seed (Sec. II-B "problem
+ * description" -> "domain decomposition").  Propagators are computed once in FP64 on the GPU
+ * and rounded to FP32; connectivity is drawn by Philox4x32-10 per (target, draw) and sorted into
+ * per-block sub-graphs, CSR by source inside each block (Eq. 5, Eq. 9-10, Sec. III-B).
+ * stream: cudaStream_t or NULL.  opts may be NULL.  On success *out owns all device memory.
+ * Errors: CORTEX_ERR_ARG (invalid parameters), CORTEX_ERR_UNSUPPORTED (sizes beyond the
+ * layout limits: in-degree or targets per block > 65535, d_max > 255), CORTEX_ERR_OOM,
+ * CORTEX_ERR_CUDA.  On error *out is NULL and nothing is leaked. */
+int cortex_build(const cortex_params* params, uint64_t seed, const cortex_options* opts,
+                 void* stream, cortex_net** out);
+
+/* Build n_nets independent networks (params[n], seeds[n]) in one handle; they are stepped
+ * together by one persistent kernel (each block owns a target range of one network).  Same
+ * errors as cortex_build. */
+int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32_t n_nets,
+                       const cortex_options* opts, void* stream, cortex_net** out);
+
+/* Advance every network by n_steps >= 0 steps from the current step (Sec. II-B loop: deliver,
+ * update, compact spikes).  Continuing in pieces gives the same result as one call.
+ * Synchronises the stream.  Errors: CORTEX_ERR_ARG, CORTEX_ERR_TIMEOUT (a grid-barrier or copy
+ * wait gave up; state is undefined but the handle can be freed), CORTEX_ERR_CUDA.  If the
+ * device raster is full, spikes keep being simulated and counted but no longer recorded, and
+ * the call returns CORTEX_ERR_OVERFLOW after finishing all steps. */
+int cortex_simulate(cortex_net* net, int64_t n_steps);
+
+/* Copy the recorded spikes of network net_idx, ordered by (step, neuron id), into caller-owned
+ * host arrays.  *n_inout: capacity on input, number of spikes on output.  If the capacity is too
+ * small, nothing is copied, *n_inout receives the needed count and CORTEX_ERR_OVERFLOW is
+ * returned.  steps/ids may be NULL when *n_inout is 0 (size query). */
+int cortex_spikes(cortex_net* net, int32_t net_idx, int64_t* n_inout, int32_t* steps,
+                  int32_t* ids);
+
+/* Forget the recorded spikes (the simulation state is unchanged). */
+int cortex_clear_spikes(cortex_net* net);
+
+/* Counters and timings (see cortex_stats_t). */
+int cortex_stats(cortex_net* net, cortex_stats_t* out);
+
+/* Incoming synapses of targets [t_begin, t_end) of network net_idx, for connectivity checks:
+ * for each synapse its source, target, delay (steps) and stored weight (as float).  Order:
+ * by target block, then source, then target.  *n_inout as in cortex_spikes. */
+int cortex_export_synapses(cortex_net* net, int32_t net_idx, int32_t t_begin, int32_t t_end,
+                           int64_t* n_inout, int32_t* src, int32_t* tgt, int32_t* delay,
+                           float* weight);
+
+/* Neuron state of network net_idx (host arrays of its n neurons): membrane potential (mV),
+ * synaptic current (pA), remaining refractory steps.  Any pointer may be NULL. */
+int cortex_get_state(cortex_net* net, int32_t net_idx, float* v, float* i_syn, int32_t* refr);
+
+/* The FP32 constants network net_idx uses, as computed on the device: out6 = {P11, P21, P22,
+ * w_exc, w_inh, j_ext}; thr = Poisson thresholds (up to 64 words), *n_thr their count,
+ * *n_ref the refractory steps. */
+int cortex_constants(cortex_net* net, int32_t net_idx, float* out6, uint32_t* thr,
+                     int32_t* n_thr, int32_t* n_ref);
+
+/* Deliver a given list of spikes of network net_idx, emitted at step t_emit, with the delivery
+ * kernel alone (measurement of the delivery path, Sec. III-B).  ids: host array of n neuron
+ * ids, any order, duplicates ignored.  The weights are added to the ring buffers exactly as in
+ * a simulation step, so the network's future input changes.  reps: number of times the launch
+ * is repeated (timing); *ms_out receives the mean device time of one launch (may be NULL);
+ * *events_out the synaptic events of one launch (may be NULL). */
+int cortex_deliver(cortex_net* net, int32_t net_idx, const int32_t* ids, int64_t n,
+                   int64_t t_emit, int32_t reps, double* ms_out, int64_t* events_out);
+
+/* Philox4x32-10 on the device for n counters (ctr: 4n words, key: 2n words, out: 4n words;
+ * host arrays).  Used to check the device generator against its published definition. */
+int cortex_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
+
+/* Release everything the handle owns.  NULL is allowed. */
+void cortex_free(cortex_net* net);
+
+/* Text of a status code; and of the calling thread's last error (empty if none). */
+const char* cortex_strerror(int code);
+const char* cortex_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CORTEX_H */

@@ -1,0 +1,815 @@
+// api.cu -- host orchestration behind the C ABI (include/cortex.h): planning of the indegree
+// sub-graph decomposition (targets per block, warps per block), device memory, the builder waves,
+// the step loop (persistent cooperative launches replayed from a CUDA graph, or split update /
+// delivery launches), and the data accessors.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cortex.h"
+#include "cortex_internal.cuh"
+
+using namespace cortex;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                                         \
+  do {                                                                                                         \
+    cudaError_t e_ = (expr);                                                                                   \
+    if (e_ != cudaSuccess) {                                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? CORTEX_ERR_OOM : CORTEX_ERR_CUDA,                          \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                                         \
+    }                                                                                                          \
+  } while (0)
+
+constexpr size_t kKeyBudget = size_t(4) << 30;  // builder scratch per wave (keys)
+
+}  // namespace
+
+struct cortex_net {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_nets = 0;
+  std::vector<cortex_params> params;
+  std::vector<uint64_t> seeds;
+  std::vector<NetDev> nets_h;
+  std::vector<BlockWork> work_h;
+  NetDev* nets_d = nullptr;
+  BlockWork* work_d = nullptr;
+  int wdtype = 0;
+  int64_t n_total = 0, total_syn = 0, total_ring = 0, total_hdr = 0, total_raster = 0;
+  // device arrays
+  void* rec_w = nullptr;
+  uint16_t* rec_tgt = nullptr;
+  uint8_t* rec_dly = nullptr;
+  uint4* hdr = nullptr;
+  float* V = nullptr;
+  float* I = nullptr;
+  int32_t* R = nullptr;
+  float* ring = nullptr;
+  uint32_t* pub_ids = nullptr;
+  uint32_t* pub_cnt = nullptr;
+  uint32_t* pub_flag = nullptr;
+  int32_t* raster_step = nullptr;
+  int32_t* raster_id = nullptr;
+  unsigned long long* raster_count = nullptr;
+  unsigned long long* events = nullptr;
+  int32_t* err = nullptr;
+  long long* step_counter = nullptr;
+  uint32_t* max_seg = nullptr;
+  std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  // plan
+  int n_warps = 8, threads = 256, n_blocks = 0, n_sm = 0;
+  int w_max = 1, w_split = 1, max_nt = 0, max_depth = 0, max_nb = 0;
+  bool ring_smem = false;
+  int mode = CORTEX_MODE_PERSISTENT;
+  int stage_bytes = 0;
+  size_t smem = 0;
+  int steps_per_launch = 1000;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  long long timeout_ns = 2000000000ll;
+  uint32_t max_seg_len = 0;
+  // bookkeeping
+  int64_t step = 0;
+  int64_t spikes_cleared = 0;
+  double build_ms = 0, sim_ms = 0;
+  int64_t sim_steps = 0, sim_events = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  template <class T>
+  cudaError_t alloc(T** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    allocs.push_back(q);
+    device_bytes += bytes;
+    *p = reinterpret_cast<T*>(q);
+    return cudaSuccess;
+  }
+
+  ~cortex_net() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (void* p : allocs) cudaFree(p);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+namespace {
+
+int validate_params(const cortex_params& p, std::string& why) {
+  if (p.n_exc < 0 || p.n_inh < 0 || (int64_t)p.n_exc + p.n_inh <= 0) return why = "neuron counts", CORTEX_ERR_ARG;
+  if ((int64_t)p.n_exc + p.n_inh > (1ll << 31) - 1) return why = "too many neurons", CORTEX_ERR_UNSUPPORTED;
+  if (p.k_exc < 0 || p.k_inh < 0) return why = "in-degree", CORTEX_ERR_ARG;
+  if ((p.k_exc > 0 && p.n_exc == 0) || (p.k_inh > 0 && p.n_inh == 0)) return why = "in-degree from an empty population", CORTEX_ERR_ARG;
+  if ((int64_t)p.k_exc + p.k_inh > 65535) return why = "in-degree above 65535", CORTEX_ERR_UNSUPPORTED;
+  if (p.d_min < 1 || p.d_max < p.d_min) return why = "delays must satisfy 1 <= d_min <= d_max", CORTEX_ERR_ARG;
+  if (p.d_max > 255) return why = "d_max above 255", CORTEX_ERR_UNSUPPORTED;
+  if (!(p.tau_m > 0) || !(p.tau_syn > 0) || !(p.c_m > 0) || !(p.dt > 0) || !(p.t_ref >= 0))
+    return why = "time constants, capacitance, dt and t_ref must be positive", CORTEX_ERR_ARG;
+  if (p.tau_m == p.tau_syn) return why = "tau_m == tau_syn (singular propagator)", CORTEX_ERR_UNSUPPORTED;
+  if (!(p.nu_ext_hz >= 0)) return why = "nu_ext_hz", CORTEX_ERR_ARG;
+  if (p.weight_dtype != CORTEX_F32 && p.weight_dtype != CORTEX_BF16) return why = "weight_dtype", CORTEX_ERR_ARG;
+  if (p.e_l != 0.0f) return why = "only E_L = 0 is supported (potentials relative to rest)", CORTEX_ERR_UNSUPPORTED;
+  return CORTEX_OK;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Targets per block for every network so that all blocks are co-resident (one per SM).
+int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb) {
+  const int cap = h->n_sm;  // one block per SM
+  const int64_t tmin = 32ll * h->n_warps;
+  int64_t n_total = 0;
+  for (auto& p : h->params) n_total += (int64_t)p.n_exc + p.n_inh;
+  int64_t T = std::max<int64_t>(tmin, ceil_div(n_total, cap));
+  if (o.targets_per_block > 0) T = std::min<int64_t>(T, o.targets_per_block);
+  for (int iter = 0; iter < 10000; ++iter) {
+    int64_t blocks = 0;
+    tb.assign(h->n_nets, 0);
+    for (int b = 0; b < h->n_nets; ++b) {
+      const int64_t n = (int64_t)h->params[b].n_exc + h->params[b].n_inh;
+      int64_t t = std::min<int64_t>(n, T);
+      // balance the blocks of one network
+      const int64_t nb = ceil_div(n, t);
+      t = ceil_div(n, nb);
+      tb[b] = (int32_t)t;
+      blocks += nb;
+    }
+    bool ok = true;
+    for (int b = 0; b < h->n_nets; ++b) ok = ok && tb[b] <= 65535;
+    if (!ok) return fail(CORTEX_ERR_UNSUPPORTED, "targets per block above 65535 (network too large for one GPU plan)");
+    if (blocks <= cap || o.targets_per_block > 0) return CORTEX_OK;
+    T = T + std::max<int64_t>(1, T / 16);
+  }
+  return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
+}
+
+int check_err(cortex_net* h, const char* where) {
+  int32_t e = 0;
+  CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (e & kErrTimeout) return fail(CORTEX_ERR_TIMEOUT, std::string(where) + ": a device wait timed out");
+  if (e & kErrBuild) return fail(CORTEX_ERR_CUDA, std::string(where) + ": builder consistency check failed");
+  if (e & kErrSegment) return fail(CORTEX_ERR_UNSUPPORTED, std::string(where) + ": a sub-graph segment exceeds the staging capacity");
+  if (e & kErrRaster) return fail(CORTEX_ERR_OVERFLOW, std::string(where) + ": raster capacity exceeded");
+  return CORTEX_OK;
+}
+
+StepArgs make_args(cortex_net* h) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nets = h->nets_d;
+  a.work = h->work_d;
+  a.n_blocks = h->n_blocks;
+  a.w_max = h->w_max;
+  a.n_total = h->n_total;
+  a.rec_w = h->rec_w;
+  a.rec_tgt = h->rec_tgt;
+  a.rec_dly = h->rec_dly;
+  a.hdr = h->hdr;
+  a.V = h->V;
+  a.I = h->I;
+  a.R = h->R;
+  a.ring = h->ring;
+  a.pub_ids = h->pub_ids;
+  a.pub_cnt = h->pub_cnt;
+  a.pub_flag = h->pub_flag;
+  a.raster_step = h->raster_step;
+  a.raster_id = h->raster_id;
+  a.raster_count = h->raster_count;
+  a.events = h->events;
+  a.err = h->err;
+  a.step_counter = h->step_counter;
+  a.stage_bytes = h->stage_bytes;
+  a.max_nt = h->max_nt;
+  a.max_depth = h->max_depth;
+  a.max_nb = h->max_nb;
+  a.timeout_ns = h->timeout_ns;
+  a.t_fixed = -1;
+  return a;
+}
+
+cudaError_t launch_persistent(cortex_net* h, int n_steps, cudaStream_t s) {
+  StepArgs a = make_args(h);
+  a.n_steps = n_steps;
+  a.phases = kPhaseUpdate | kPhaseDeliver | kPhaseBarrier;
+  a.ring_smem = h->ring_smem ? 1 : 0;
+  return launch_step(a, h->n_blocks, h->threads, h->smem, true, s);
+}
+
+cudaError_t launch_split_window(cortex_net* h, int wn, cudaStream_t s) {
+  StepArgs a = make_args(h);
+  a.n_steps = wn;
+  a.ring_smem = 0;
+  a.phases = kPhaseUpdate;
+  cudaError_t e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s);
+  if (e != cudaSuccess) return e;
+  a.phases = kPhaseDeliver;
+  e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s);
+  if (e != cudaSuccess) return e;
+  return launch_advance_split(a, h->n_nets, wn, s);
+}
+
+// Capture one chunk of the step loop in a CUDA graph (persistent: one cooperative launch of
+// steps_per_launch steps; split: as many windows as fit in the same number of steps).
+int ensure_graph(cortex_net* h) {
+  if (h->graph) return CORTEX_OK;
+  // capture on a private stream (the legacy default stream cannot be captured); the graph is
+  // then launched on the handle's stream
+  cudaStream_t cs = nullptr;
+  CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    h->use_graph = false;
+    return CORTEX_OK;
+  }
+  if (h->mode == CORTEX_MODE_PERSISTENT) {
+    e = launch_persistent(h, h->steps_per_launch, cs);
+  } else {
+    for (int s = 0; s + h->w_split <= h->steps_per_launch && e == cudaSuccess; s += h->w_split)
+      e = launch_split_window(h, h->w_split, cs);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    h->use_graph = false;  // fall back to direct launches
+    return CORTEX_OK;
+  }
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->graph = nullptr;
+    h->use_graph = false;
+    return CORTEX_OK;
+  }
+  h->graph_steps = (h->mode == CORTEX_MODE_PERSISTENT) ? h->steps_per_launch
+                                                       : (h->steps_per_launch / h->w_split) * h->w_split;
+  return CORTEX_OK;
+}
+
+int build_network(cortex_net* h, int b, const std::vector<int32_t>& tb) {
+  const NetDev& nd = h->nets_h[b];
+  const int64_t n = nd.n;
+  const int nbk = nd.n_blocks;
+  // waves of blocks bounded by the key budget
+  const int64_t keys_per_block = (int64_t)tb[b] * nd.k;
+  int per_wave = (int)std::max<int64_t>(1, std::min<int64_t>(nbk, (int64_t)(kKeyBudget / 4) / std::max<int64_t>(1, keys_per_block)));
+  // counters: 2 x per_wave x n words
+  while (per_wave > 1 && (size_t)per_wave * n * 8 > kKeyBudget) per_wave /= 2;
+  uint32_t *cnt = nullptr, *cursor = nullptr, *keys = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&cnt, (size_t)per_wave * n * 4, h->stream));
+  CUDA_TRY(cudaMallocAsync((void**)&cursor, (size_t)per_wave * n * 4, h->stream));
+  CUDA_TRY(cudaMallocAsync((void**)&keys, (size_t)std::max<int64_t>(1, per_wave * keys_per_block) * 4, h->stream));
+  int rc = CORTEX_OK;
+  for (int g0 = 0; g0 < nbk && rc == CORTEX_OK; g0 += per_wave) {
+    const int ng = std::min(per_wave, nbk - g0);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)ng * n * 4, h->stream);
+    if (e == cudaSuccess) e = launch_build_count_net(h->nets_d, b, (int32_t)n, g0, ng, tb[b], cnt, h->stream);
+    if (e == cudaSuccess) e = launch_scan_groups(cnt, cursor, ng, (int32_t)n, nullptr, h->stream);
+    if (e == cudaSuccess) e = launch_build_fill_net(h->nets_d, b, (int32_t)n, g0, ng, tb[b], cursor, keys, h->stream);
+    if (e == cudaSuccess)
+      e = launch_build_finalize_net(h->nets_d, h->work_d, b, g0, ng, h->n_warps, cnt, cursor, keys, h->rec_w,
+                                    h->rec_tgt, h->rec_dly, h->hdr, h->err, h->max_seg, h->stream);
+    if (e != cudaSuccess) rc = fail(CORTEX_ERR_CUDA, std::string("builder: ") + cudaGetErrorString(e));
+  }
+  cudaFreeAsync(cnt, h->stream);
+  cudaFreeAsync(cursor, h->stream);
+  cudaFreeAsync(keys, h->stream);
+  return rc;
+}
+
+int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
+  const int smem_cap = (int)prop.sharedMemPerBlockOptin - 1024;  // leave room for static shared memory
+  const int wsz = h->wdtype == CORTEX_BF16 ? 2 : 4;
+  const int need_stage = (int)h->max_seg_len * (wsz + 3) + 3 * 32 + 64;
+  const int want_stage = std::max(need_stage, 48 * 1024);
+  const size_t base = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, false, 0);
+  const size_t ring_bytes = (size_t)h->max_depth * h->max_nt * 4;
+  bool smem_ring;
+  if (o.ring == CORTEX_RING_SMEM) smem_ring = true;
+  else if (o.ring == CORTEX_RING_GLOBAL) smem_ring = false;
+  else smem_ring = base + ring_bytes + (size_t)want_stage <= (size_t)smem_cap;
+  if (h->mode == CORTEX_MODE_SPLIT) smem_ring = false;
+  const size_t fixed = base + (smem_ring ? ring_bytes : 0);
+  if (fixed + (size_t)need_stage > (size_t)smem_cap)
+    return fail(CORTEX_ERR_UNSUPPORTED, "shared memory too small for this plan (ring " + std::to_string(ring_bytes) +
+                                            " B, state " + std::to_string(base) + " B, staging " +
+                                            std::to_string(need_stage) + " B)");
+  int stage = (int)std::min<size_t>((size_t)smem_cap - fixed, 96 * 1024);
+  stage = std::max(stage, need_stage) & ~127;
+  h->ring_smem = smem_ring;
+  h->stage_bytes = stage;
+  h->smem = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, smem_ring, stage);
+  CUDA_TRY(step_kernel_attributes(h->smem));
+  return CORTEX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cortex_strerror(int code) {
+  switch (code) {
+    case CORTEX_OK: return "ok";
+    case CORTEX_ERR_ARG: return "invalid argument";
+    case CORTEX_ERR_OOM: return "out of memory";
+    case CORTEX_ERR_CUDA: return "CUDA error";
+    case CORTEX_ERR_TIMEOUT: return "device wait timed out";
+    case CORTEX_ERR_UNSUPPORTED: return "unsupported size or configuration";
+    case CORTEX_ERR_OVERFLOW: return "buffer too small";
+    default: return "unknown status";
+  }
+}
+
+const char* cortex_last_error(void) { return g_last_error.c_str(); }
+
+void cortex_free(cortex_net* net) {
+  if (!net) return;
+  if (net->stream) cudaStreamSynchronize(net->stream);
+  delete net;
+}
+
+int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32_t n_nets, const cortex_options* opts,
+                       void* stream, cortex_net** out) {
+  if (!out) return fail(CORTEX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!params || !seeds || n_nets <= 0) return fail(CORTEX_ERR_ARG, "params, seeds, n_nets");
+  cortex_options o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  for (int b = 0; b < n_nets; ++b) {
+    std::string why;
+    int rc = validate_params(params[b], why);
+    if (rc != CORTEX_OK) return fail(rc, "network " + std::to_string(b) + ": " + why);
+    if (params[b].weight_dtype != params[0].weight_dtype)
+      return fail(CORTEX_ERR_UNSUPPORTED, "all networks of a batch must use the same weight_dtype");
+  }
+  if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..14");
+  if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
+  if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
+
+  cortex_net* h = new (std::nothrow) cortex_net();
+  if (!h) return fail(CORTEX_ERR_OOM, "handle");
+  auto bail = [&](int rc) {
+    delete h;
+    return rc;
+  };
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(CORTEX_ERR_UNSUPPORTED, "no CUDA device"));
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(fail(CORTEX_ERR_CUDA, "device properties"));
+  if (prop.major < 10) return bail(fail(CORTEX_ERR_UNSUPPORTED, "needs a Blackwell GPU (sm_103a build)"));
+  h->n_sm = prop.multiProcessorCount;
+  h->n_nets = n_nets;
+  h->params.assign(params, params + n_nets);
+  h->seeds.assign(seeds, seeds + n_nets);
+  h->wdtype = params[0].weight_dtype;
+  h->n_warps = o.warps_per_block ? o.warps_per_block : 8;
+  h->threads = 32 * h->n_warps;
+  h->mode = o.mode;
+  h->steps_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 1000;
+  h->use_graph = o.use_graph >= 0;
+  if (o.barrier_timeout_ms > 0) h->timeout_ns = (long long)(o.barrier_timeout_ms * 1e6);
+
+  std::vector<int32_t> tb;
+  int rc = plan_blocks(h, o, tb);
+  if (rc != CORTEX_OK) return bail(rc);
+
+  // networks and the work table
+  h->w_max = 1;
+  h->w_split = 1 << 30;
+  int64_t neuron_base = 0, rec = 0, hdr = 0, ring = 0, raster = 0;
+  for (int b = 0; b < n_nets; ++b) {
+    const cortex_params& p = params[b];
+    NetDev d;
+    memset(&d, 0, sizeof(d));
+    d.n_exc = p.n_exc;
+    d.n_inh = p.n_inh;
+    d.n = p.n_exc + p.n_inh;
+    d.k_exc = p.k_exc;
+    d.k_inh = p.k_inh;
+    d.k = p.k_exc + p.k_inh;
+    d.d_min = p.d_min;
+    d.d_max = p.d_max;
+    d.depth = p.d_max;
+    d.window = p.d_min;
+    d.seed_lo = (uint32_t)seeds[b];
+    d.seed_hi = (uint32_t)(seeds[b] >> 32);
+    d.wdtype = p.weight_dtype;
+    d.v_th = p.v_th;
+    d.v_reset = p.v_reset;
+    d.j_ext = p.j_ext;
+    d.tau_m = p.tau_m;
+    d.c_m = p.c_m;
+    d.tau_syn = p.tau_syn;
+    d.t_ref = p.t_ref;
+    d.dt = p.dt;
+    d.nu_ext_hz = p.nu_ext_hz;
+    d.j_exc_in = p.j_exc;
+    d.j_inh_in = p.j_inh;
+    d.neuron_base = neuron_base;
+    const int nbk = (int)ceil_div(d.n, tb[b]);
+    d.first_block = (int)h->work_h.size();
+    d.n_blocks = nbk;
+    const int64_t rcap = o.raster_capacity > 0 ? o.raster_capacity : std::max<int64_t>(1 << 20, 16ll * d.n);
+    d.raster_base = raster;
+    d.raster_cap = rcap;
+    raster += rcap;
+    const int32_t tw = (int32_t)ceil_div(tb[b], h->n_warps);
+    for (int g = 0; g < nbk; ++g) {
+      BlockWork w;
+      memset(&w, 0, sizeof(w));
+      w.net = b;
+      w.group = g;
+      w.t0 = g * tb[b];
+      w.nt = std::min<int32_t>(tb[b], d.n - w.t0);
+      w.tw = tw;
+      w.n_src = d.n;
+      w.rec_base = rec;
+      w.hdr_base = hdr;
+      w.ring_base = ring;
+      w.pub_base = neuron_base + w.t0;
+      rec += (int64_t)w.nt * d.k;
+      hdr += d.n;
+      ring += (int64_t)d.depth * w.nt;
+      h->work_h.push_back(w);
+      h->max_nt = std::max(h->max_nt, w.nt);
+    }
+    h->max_nb = std::max(h->max_nb, nbk);
+    h->max_depth = std::max(h->max_depth, d.depth);
+    h->w_max = std::max(h->w_max, d.window);
+    h->w_split = std::min(h->w_split, d.window);
+    neuron_base += d.n;
+    h->nets_h.push_back(d);
+  }
+  h->n_blocks = (int)h->work_h.size();
+  h->n_total = neuron_base;
+  h->total_syn = rec;
+  h->total_hdr = hdr;
+  h->total_ring = ring;
+  h->total_raster = raster;
+
+  cudaStream_t s = h->stream;
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
+    return bail(fail(CORTEX_ERR_CUDA, "events"));
+  auto A = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return CORTEX_OK;
+    return fail(e == cudaErrorMemoryAllocation ? CORTEX_ERR_OOM : CORTEX_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  };
+#define TRY(e, what)                 \
+  do {                               \
+    int r_ = A((e), (what));         \
+    if (r_ != CORTEX_OK) return bail(r_); \
+  } while (0)
+
+  const size_t wsz = h->wdtype == CORTEX_BF16 ? 2 : 4;
+  TRY(h->alloc(&h->nets_d, sizeof(NetDev) * n_nets), "alloc nets");
+  TRY(h->alloc(&h->work_d, sizeof(BlockWork) * h->n_blocks), "alloc work");
+  TRY(h->alloc(&h->rec_w, wsz * h->total_syn + 64), "alloc weights");
+  TRY(h->alloc(&h->rec_tgt, 2 * h->total_syn + 64), "alloc targets");
+  TRY(h->alloc(&h->rec_dly, h->total_syn + 64), "alloc delays");
+  TRY(h->alloc(&h->hdr, 32 * h->total_hdr), "alloc headers");
+  TRY(h->alloc(&h->V, 4 * h->n_total), "alloc V");
+  TRY(h->alloc(&h->I, 4 * h->n_total), "alloc I");
+  TRY(h->alloc(&h->R, 4 * h->n_total), "alloc R");
+  TRY(h->alloc(&h->ring, 4 * h->total_ring), "alloc ring");
+  TRY(h->alloc(&h->pub_ids, 4 * (size_t)2 * h->w_max * h->n_total), "alloc spike lists");
+  TRY(h->alloc(&h->pub_cnt, 4 * (size_t)2 * h->w_max * h->n_blocks), "alloc spike counts");
+  TRY(h->alloc(&h->pub_flag, 4 * (size_t)h->n_blocks), "alloc flags");
+  TRY(h->alloc(&h->raster_step, 4 * h->total_raster), "alloc raster");
+  TRY(h->alloc(&h->raster_id, 4 * h->total_raster), "alloc raster");
+  TRY(h->alloc(&h->raster_count, 8 * (size_t)n_nets), "alloc counters");
+  TRY(h->alloc(&h->events, 8 * (size_t)n_nets), "alloc counters");
+  TRY(h->alloc(&h->err, 16), "alloc err");
+  TRY(h->alloc(&h->step_counter, 16), "alloc step");
+  TRY(h->alloc(&h->max_seg, 16), "alloc max_seg");
+
+  TRY(cudaEventRecord(h->ev0, s), "event");
+  TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * n_nets, cudaMemcpyHostToDevice, s), "upload nets");
+  TRY(cudaMemcpyAsync(h->work_d, h->work_h.data(), sizeof(BlockWork) * h->n_blocks, cudaMemcpyHostToDevice, s), "upload work");
+  TRY(cudaMemsetAsync(h->err, 0, 16, s), "memset");
+  TRY(cudaMemsetAsync(h->max_seg, 0, 16, s), "memset");
+  TRY(cudaMemsetAsync(h->step_counter, 0, 16, s), "memset");
+  TRY(launch_props(h->nets_d, n_nets, s), "propagators");
+  TRY(cudaMemcpyAsync(h->nets_h.data(), h->nets_d, sizeof(NetDev) * n_nets, cudaMemcpyDeviceToHost, s), "download nets");
+  TRY(cudaStreamSynchronize(s), "sync");
+  for (int b = 0; b < n_nets; ++b)
+    if (h->nets_h[b].n_thr < 1) return bail(fail(CORTEX_ERR_UNSUPPORTED, "Poisson rate too high for the threshold table"));
+
+  for (int b = 0; b < n_nets; ++b) {
+    rc = build_network(h, b, tb);
+    if (rc != CORTEX_OK) return bail(rc);
+    TRY(launch_init_state(&h->nets_h[b], h->nets_d, b, h->V, h->I, h->R, s), "init state");
+  }
+  TRY(cudaMemsetAsync(h->ring, 0, 4 * h->total_ring, s), "memset ring");
+  TRY(cudaMemsetAsync(h->pub_flag, 0, 4 * (size_t)h->n_blocks, s), "memset flags");
+  TRY(cudaMemsetAsync(h->pub_cnt, 0, 4 * (size_t)2 * h->w_max * h->n_blocks, s), "memset counts");
+  TRY(cudaMemsetAsync(h->raster_count, 0, 8 * (size_t)n_nets, s), "memset");
+  TRY(cudaMemsetAsync(h->events, 0, 8 * (size_t)n_nets, s), "memset");
+  TRY(cudaMemcpyAsync(&h->max_seg_len, h->max_seg, 4, cudaMemcpyDeviceToHost, s), "download");
+  TRY(cudaEventRecord(h->ev1, s), "event");
+  rc = check_err(h, "build");
+  if (rc != CORTEX_OK) return bail(rc);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->build_ms = ms;
+
+  rc = choose_stage_and_ring(h, o);
+  if (rc != CORTEX_OK) return bail(rc);
+  if (h->mode == CORTEX_MODE_PERSISTENT) {
+    const int occ = step_occupancy(h->threads, h->smem);
+    if (occ * h->n_sm < h->n_blocks) {
+      if (o.mode == CORTEX_MODE_PERSISTENT && opts && opts->mode == CORTEX_MODE_PERSISTENT && o.ring == CORTEX_RING_SMEM)
+        return bail(fail(CORTEX_ERR_UNSUPPORTED, "blocks cannot all be resident for the persistent kernel"));
+      h->mode = CORTEX_MODE_SPLIT;  // not co-resident: fall back to split launches
+      rc = choose_stage_and_ring(h, o);
+      if (rc != CORTEX_OK) return bail(rc);
+    }
+  }
+#undef TRY
+  *out = h;
+  return CORTEX_OK;
+}
+
+int cortex_build(const cortex_params* params, uint64_t seed, const cortex_options* opts, void* stream,
+                 cortex_net** out) {
+  return cortex_build_batch(params, &seed, 1, opts, stream, out);
+}
+
+int cortex_simulate(cortex_net* h, int64_t n_steps) {
+  if (!h || n_steps < 0) return fail(CORTEX_ERR_ARG, "cortex_simulate: handle / n_steps");
+  unsigned long long ev_before = 0;
+  {
+    std::vector<unsigned long long> e(h->n_nets);
+    CUDA_TRY(cudaMemcpyAsync(e.data(), h->events, 8 * h->n_nets, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (auto x : e) ev_before += x;
+  }
+  CUDA_TRY(cudaMemsetAsync(h->err, 0, 4, h->stream));
+  CUDA_TRY(cudaEventRecord(h->ev0, h->stream));
+  int64_t left = n_steps;
+  if (h->use_graph && left >= h->steps_per_launch) {
+    int rc = ensure_graph(h);
+    if (rc != CORTEX_OK) return rc;
+  }
+  while (left > 0) {
+    if (h->use_graph && h->graph && left >= h->graph_steps && h->graph_steps > 0) {
+      CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+      left -= h->graph_steps;
+      continue;
+    }
+    if (h->mode == CORTEX_MODE_PERSISTENT) {
+      const int n = (int)std::min<int64_t>(left, h->steps_per_launch);
+      CUDA_TRY(launch_persistent(h, n, h->stream));
+      left -= n;
+    } else {
+      const int wn = (int)std::min<int64_t>(left, h->w_split);
+      CUDA_TRY(launch_split_window(h, wn, h->stream));
+      left -= wn;
+    }
+  }
+  CUDA_TRY(cudaEventRecord(h->ev1, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->sim_ms = ms;
+  h->sim_steps = n_steps;
+  h->step += n_steps;
+  unsigned long long ev_after = 0;
+  {
+    std::vector<unsigned long long> e(h->n_nets);
+    CUDA_TRY(cudaMemcpy(e.data(), h->events, 8 * h->n_nets, cudaMemcpyDeviceToHost));
+    for (auto x : e) ev_after += x;
+  }
+  h->sim_events = (int64_t)(ev_after - ev_before);
+  return check_err(h, "simulate");
+}
+
+int cortex_spikes(cortex_net* h, int32_t net_idx, int64_t* n_inout, int32_t* steps, int32_t* ids) {
+  if (!h || !n_inout || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_spikes: arguments");
+  unsigned long long c = 0;
+  CUDA_TRY(cudaMemcpyAsync(&c, h->raster_count + net_idx, 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const NetDev& d = h->nets_h[net_idx];
+  const int64_t n = std::min<int64_t>((int64_t)c, d.raster_cap);
+  if (*n_inout < n) {
+    *n_inout = n;
+    return fail(CORTEX_ERR_OVERFLOW, "cortex_spikes: capacity too small");
+  }
+  *n_inout = n;
+  if (n == 0) return CORTEX_OK;
+  if (!steps || !ids) return fail(CORTEX_ERR_ARG, "cortex_spikes: NULL output");
+  CUDA_TRY(cudaMemcpyAsync(steps, h->raster_step + d.raster_base, 4 * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(ids, h->raster_id + d.raster_base, 4 * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_clear_spikes(cortex_net* h) {
+  if (!h) return fail(CORTEX_ERR_ARG, "handle");
+  std::vector<unsigned long long> c(h->n_nets);
+  CUDA_TRY(cudaMemcpyAsync(c.data(), h->raster_count, 8 * h->n_nets, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (auto x : c) h->spikes_cleared += (int64_t)x;
+  CUDA_TRY(cudaMemsetAsync(h->raster_count, 0, 8 * h->n_nets, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_stats(cortex_net* h, cortex_stats_t* st) {
+  if (!h || !st) return fail(CORTEX_ERR_ARG, "cortex_stats: arguments");
+  memset(st, 0, sizeof(*st));
+  std::vector<unsigned long long> c(h->n_nets), e(h->n_nets);
+  CUDA_TRY(cudaMemcpyAsync(c.data(), h->raster_count, 8 * h->n_nets, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(e.data(), h->events, 8 * h->n_nets, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  st->n_nets = h->n_nets;
+  st->n_neurons = h->n_total;
+  st->n_synapses = h->total_syn;
+  st->step = h->step;
+  st->spikes = h->spikes_cleared;
+  for (auto x : c) st->spikes += (int64_t)x;
+  for (auto x : e) st->events += (int64_t)x;
+  st->build_ms = h->build_ms;
+  st->simulate_ms = h->sim_ms;
+  st->simulate_steps = h->sim_steps;
+  st->simulate_events = h->sim_events;
+  st->n_blocks = h->n_blocks;
+  st->threads_per_block = h->threads;
+  st->ring_in_smem = h->ring_smem ? 1 : 0;
+  st->mode = h->mode;
+  st->device_bytes = (int64_t)h->device_bytes;
+  return CORTEX_OK;
+}
+
+int cortex_get_state(cortex_net* h, int32_t net_idx, float* v, float* i_syn, int32_t* refr) {
+  if (!h || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_get_state: arguments");
+  const NetDev& d = h->nets_h[net_idx];
+  if (v) CUDA_TRY(cudaMemcpyAsync(v, h->V + d.neuron_base, 4ull * d.n, cudaMemcpyDeviceToHost, h->stream));
+  if (i_syn) CUDA_TRY(cudaMemcpyAsync(i_syn, h->I + d.neuron_base, 4ull * d.n, cudaMemcpyDeviceToHost, h->stream));
+  if (refr) CUDA_TRY(cudaMemcpyAsync(refr, h->R + d.neuron_base, 4ull * d.n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_constants(cortex_net* h, int32_t net_idx, float* out6, uint32_t* thr, int32_t* n_thr, int32_t* n_ref) {
+  if (!h || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_constants: arguments");
+  const NetDev& d = h->nets_h[net_idx];
+  if (out6) {
+    out6[0] = d.p11;
+    out6[1] = d.p21;
+    out6[2] = d.p22;
+    out6[3] = d.w_exc;
+    out6[4] = d.w_inh;
+    out6[5] = d.j_ext;
+  }
+  if (thr)
+    for (int k = 0; k < d.n_thr; ++k) thr[k] = d.thr[k];
+  if (n_thr) *n_thr = d.n_thr;
+  if (n_ref) *n_ref = d.n_ref;
+  return CORTEX_OK;
+}
+
+int cortex_export_synapses(cortex_net* h, int32_t net_idx, int32_t t_begin, int32_t t_end, int64_t* n_inout,
+                           int32_t* src, int32_t* tgt, int32_t* delay, float* weight) {
+  if (!h || !n_inout || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_export_synapses: arguments");
+  const NetDev& d = h->nets_h[net_idx];
+  if (t_begin < 0 || t_end > d.n || t_begin > t_end) return fail(CORTEX_ERR_ARG, "cortex_export_synapses: target range");
+  const int64_t need = (int64_t)(t_end - t_begin) * d.k;
+  if (*n_inout < need) {
+    *n_inout = need;
+    return fail(CORTEX_ERR_OVERFLOW, "cortex_export_synapses: capacity too small");
+  }
+  *n_inout = need;
+  if (need == 0) return CORTEX_OK;
+  int32_t *ds = nullptr, *dt = nullptr, *dd = nullptr;
+  float* dw = nullptr;
+  unsigned long long* cnt = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&ds, 4 * need, h->stream));
+  CUDA_TRY(cudaMallocAsync((void**)&dt, 4 * need, h->stream));
+  CUDA_TRY(cudaMallocAsync((void**)&dd, 4 * need, h->stream));
+  CUDA_TRY(cudaMallocAsync((void**)&dw, 4 * need, h->stream));
+  CUDA_TRY(cudaMallocAsync((void**)&cnt, 8, h->stream));
+  CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, h->stream));
+  for (int g = 0; g < d.n_blocks; ++g) {
+    const BlockWork& w = h->work_h[d.first_block + g];
+    if (w.t0 + w.nt <= t_begin || w.t0 >= t_end) continue;
+    CUDA_TRY(launch_export(h->work_d, d.first_block + g, w.t0, h->rec_w, d.wdtype, h->rec_tgt, h->rec_dly, h->hdr, d.n,
+                           t_begin, t_end, cnt, ds, dt, dd, dw, need, h->stream));
+  }
+  unsigned long long got = 0;
+  std::vector<int32_t> hs(need), ht(need), hd(need);
+  std::vector<float> hw(need);
+  CUDA_TRY(cudaMemcpyAsync(&got, cnt, 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(hs.data(), ds, 4 * need, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(ht.data(), dt, 4 * need, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(hd.data(), dd, 4 * need, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(hw.data(), dw, 4 * need, cudaMemcpyDeviceToHost, h->stream));
+  cudaFreeAsync(ds, h->stream);
+  cudaFreeAsync(dt, h->stream);
+  cudaFreeAsync(dd, h->stream);
+  cudaFreeAsync(dw, h->stream);
+  cudaFreeAsync(cnt, h->stream);
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if ((int64_t)got != need) return fail(CORTEX_ERR_CUDA, "cortex_export_synapses: synapse count mismatch");
+  // canonical order: (target, source, delay)
+  std::vector<int64_t> idx(need);
+  for (int64_t q = 0; q < need; ++q) idx[q] = q;
+  std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
+    if (ht[x] != ht[y]) return ht[x] < ht[y];
+    if (hs[x] != hs[y]) return hs[x] < hs[y];
+    return hd[x] < hd[y];
+  });
+  for (int64_t q = 0; q < need; ++q) {
+    if (src) src[q] = hs[idx[q]];
+    if (tgt) tgt[q] = ht[idx[q]];
+    if (delay) delay[q] = hd[idx[q]];
+    if (weight) weight[q] = hw[idx[q]];
+  }
+  return CORTEX_OK;
+}
+
+int cortex_deliver(cortex_net* h, int32_t net_idx, const int32_t* ids, int64_t n, int64_t t_emit, int32_t reps,
+                   double* ms_out, int64_t* events_out) {
+  if (!h || net_idx < 0 || net_idx >= h->n_nets || n < 0 || (n > 0 && !ids) || t_emit < 0 || reps < 1)
+    return fail(CORTEX_ERR_ARG, "cortex_deliver: arguments");
+  const NetDev& d = h->nets_h[net_idx];
+  std::vector<int32_t> v(ids, ids + n);
+  for (int32_t x : v)
+    if (x < 0 || x >= d.n) return fail(CORTEX_ERR_ARG, "cortex_deliver: neuron id out of range");
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+  // publication slots (parity 0, window step 0): ids of each block's range, counts per block
+  std::vector<uint32_t> cnt(h->n_blocks, 0);
+  const int32_t tb = h->work_h[d.first_block].nt;
+  std::vector<uint32_t> slots(d.n, 0);
+  for (int32_t x : v) {
+    const int g = x / tb;
+    slots[(int64_t)g * tb + cnt[d.first_block + g]] = (uint32_t)x;
+    cnt[d.first_block + g] += 1;
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->pub_cnt, cnt.data(), 4 * h->n_blocks, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->pub_ids + d.neuron_base, slots.data(), 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->err, 0, 4, h->stream));
+  unsigned long long e0 = 0, e1 = 0;
+  CUDA_TRY(cudaMemcpyAsync(&e0, h->events + net_idx, 8, cudaMemcpyDeviceToHost, h->stream));
+  StepArgs a = make_args(h);
+  a.n_steps = 1;
+  a.phases = kPhaseDeliver;
+  a.ring_smem = 0;
+  a.raster_step = nullptr;
+  a.raster_id = nullptr;
+  a.t_fixed = t_emit;
+  CUDA_TRY(cudaEventRecord(h->ev0, h->stream));
+  for (int r = 0; r < reps; ++r) CUDA_TRY(launch_step(a, h->n_blocks, h->threads, h->smem, false, h->stream));
+  CUDA_TRY(cudaEventRecord(h->ev1, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(&e1, h->events + net_idx, 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  if (ms_out) *ms_out = ms / reps;
+  if (events_out) *events_out = (int64_t)((e1 - e0) / (unsigned long long)reps);
+  return check_err(h, "deliver");
+}
+
+int cortex_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(CORTEX_ERR_ARG, "cortex_philox: arguments");
+  if (n == 0) return CORTEX_OK;
+  uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+  CUDA_TRY(cudaMalloc(&dc, 16 * n));
+  CUDA_TRY(cudaMalloc(&dk, 8 * n));
+  CUDA_TRY(cudaMalloc(&dout, 16 * n));
+  CUDA_TRY(cudaMemcpy(dc, ctr, 16 * n, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(dk, key, 8 * n, cudaMemcpyHostToDevice));
+  CUDA_TRY(launch_philox(dc, dk, n, dout, nullptr));
+  CUDA_TRY(cudaMemcpy(out, dout, 16 * n, cudaMemcpyDeviceToHost));
+  cudaFree(dc);
+  cudaFree(dk);
+  cudaFree(dout);
+  return CORTEX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,375 @@
+// build.cu -- one-time device work: propagators (FP64), initial state, and the network builder
+// that turns Philox draws into per-block sub-graphs stored as CSR by source (Eq. 5, Eq. 9-10,
+// Sec. III-B: each block owns a contiguous range of post-synaptic neurons and all of their
+// incoming synapses; inside the block the synapses of one source are contiguous and sorted by
+// target, hence by owning warp).
+//
+// Builder passes for a wave of blocks of one network:
+//   count     every (target, draw) increments cnt[block][source]              (integer atomics)
+//   scan      cursor[block][*] = exclusive prefix of cnt[block][*]
+//   fill      key = (local target << 16 | draw) placed at cursor[block][source]++
+//   finalize  one warp per (block, source) segment: sort the keys, regenerate source and delay
+//             from Philox, write the SoA records and the segment header
+#include <algorithm>
+#include "cortex_internal.cuh"
+
+namespace cortex {
+
+// ---- propagators and Poisson thresholds (FP64, once) ----------------------------------------
+// Exact integration of Eq. 1 with an exponential current (Eq. 3 as a current synapse):
+//   P22 = exp(-h/tau_m), P11 = exp(-h/tau_syn), P21 = tau_m tau_syn / (C (tau_syn - tau_m)) (P11 - P22)
+// Poisson(lambda = nu_ext dt) thresholds thr[k] = floor(2^32 P(X <= k)), saturating at 2^32 - 1.
+__global__ void k_props(NetDev* nets, int n_nets) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_nets) return;
+  NetDev& d = nets[b];
+  const double h = (double)d.dt, tm = (double)d.tau_m, ts = (double)d.tau_syn, c = (double)d.c_m;
+  const double p22 = exp(-h / tm);
+  const double p11 = exp(-h / ts);
+  const double p21 = tm * ts / (c * (ts - tm)) * (p11 - p22);
+  d.p11 = (float)p11;
+  d.p21 = (float)p21;
+  d.p22 = (float)p22;
+  d.n_ref = (int32_t)llround((double)d.t_ref / h);
+  const double lam = (double)d.nu_ext_hz * (double)d.dt / 1000.0;
+  double pmf = exp(-lam), cdf = pmf;
+  int n = -1;
+  for (int k = 0; k < kPoissonCap; ++k) {
+    if (k > 0) {
+      pmf = pmf * lam / (double)k;
+      cdf = cdf + pmf;
+    }
+    const double x = cdf * 4294967296.0;
+    if (x >= 4294967295.0) {
+      d.thr[k] = 0xffffffffu;
+      n = k + 1;
+      break;
+    }
+    d.thr[k] = (uint32_t)floor(x);
+  }
+  d.n_thr = n;  // -1: table did not saturate (rejected by the host)
+  if (d.wdtype == 1) {
+    d.w_exc = __bfloat162float(__float2bfloat16_rn(d.j_exc_in));
+    d.w_inh = __bfloat162float(__float2bfloat16_rn(d.j_inh_in));
+  } else {
+    d.w_exc = d.j_exc_in;
+    d.w_inh = d.j_inh_in;
+  }
+}
+
+cudaError_t launch_props(NetDev* nets, int n_nets, cudaStream_t s) {
+  k_props<<<(n_nets + 63) / 64, 64, 0, s>>>(nets, n_nets);
+  return cudaGetLastError();
+}
+
+// ---- draws ---------------------------------------------------------------------------------
+// Draw j of target i: Philox(ctr = (i, j/2, 1, 0), key = seed) gives two draws per call; words
+// (x, y) for even j, (z, w) for odd j.  Source from the first word (E for j < K_E, else I),
+// delay d_min + floor(word2 * (d_max - d_min + 1) / 2^32).
+struct Draw2 {
+  uint32_t src[2];
+  uint32_t dly[2];
+};
+
+__device__ __forceinline__ Draw2 draw_pair(const NetDev& d, uint32_t i, uint32_t pair) {
+  const uint4 r = philox4x32_10(make_uint4(i, pair, kStreamConn, 0u), d.seed_lo, d.seed_hi);
+  Draw2 out;
+  const uint32_t nd = (uint32_t)(d.d_max - d.d_min + 1);
+  const uint32_t j0 = 2u * pair, j1 = j0 + 1u;
+  out.src[0] = (j0 < (uint32_t)d.k_exc) ? scale32(r.x, (uint32_t)d.n_exc) : (uint32_t)d.n_exc + scale32(r.x, (uint32_t)d.n_inh);
+  out.dly[0] = (uint32_t)d.d_min + scale32(r.y, nd);
+  out.src[1] = (j1 < (uint32_t)d.k_exc) ? scale32(r.z, (uint32_t)d.n_exc) : (uint32_t)d.n_exc + scale32(r.z, (uint32_t)d.n_inh);
+  out.dly[1] = (uint32_t)d.d_min + scale32(r.w, nd);
+  return out;
+}
+
+// Targets of a wave: [t_lo, t_hi) of the network; block of target i = i / tb.
+__global__ void k_count(const NetDev* __restrict__ nets, int net_idx, int32_t t_lo, int32_t t_hi, int32_t tb,
+                        int first_group, uint32_t* __restrict__ cnt) {
+  const NetDev d = nets[net_idx];
+  const int64_t pairs = (d.k + 1) / 2;
+  const int64_t total = (int64_t)(t_hi - t_lo) * pairs;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(t_lo + q / pairs);
+    const uint32_t p = (uint32_t)(q % pairs);
+    const Draw2 dr = draw_pair(d, i, p);
+    const int64_t g = (int64_t)(i / tb) - first_group;
+    atomicAdd(&cnt[g * d.n + dr.src[0]], 1u);
+    if (2 * p + 1 < (uint32_t)d.k) atomicAdd(&cnt[g * d.n + dr.src[1]], 1u);
+  }
+}
+
+cudaError_t launch_build_count_net(const NetDev* nets_dev, int net_idx, int32_t n, int first_group, int n_groups,
+                                   int32_t tb, uint32_t* cnt, cudaStream_t s) {
+  const int32_t t_lo = first_group * tb;
+  const int32_t t_hi = min(n, (first_group + n_groups) * tb);
+  k_count<<<152 * 8, 256, 0, s>>>(nets_dev, net_idx, t_lo, t_hi, tb, first_group, cnt);
+  return cudaGetLastError();
+}
+
+// ---- per-block exclusive scan over the sources -------------------------------------------
+__global__ void k_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ cursor, int32_t n_src) {
+  __shared__ uint32_t warp_sum[32];
+  __shared__ uint32_t carry;
+  const int64_t base = (int64_t)blockIdx.x * n_src;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int64_t off = 0; off < n_src; off += blockDim.x) {
+    const int64_t s = off + threadIdx.x;
+    const uint32_t v = (s < n_src) ? cnt[base + s] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = (lane < nwarps) ? warp_sum[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nwarps) warp_sum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t before = carry + (warp > 0 ? warp_sum[warp - 1] : 0u) + x - v;
+    if (s < n_src) cursor[base + s] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[nwarps - 1];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_scan_groups(uint32_t* cnt, uint32_t* cursor, int n_groups, int32_t n_src, uint32_t*, cudaStream_t s) {
+  k_scan<<<n_groups, 1024, 0, s>>>(cnt, cursor, n_src);
+  return cudaGetLastError();
+}
+
+// ---- fill: scatter keys into their (block, source) segments --------------------------------
+__global__ void k_fill(const NetDev* __restrict__ nets, int net_idx, int32_t t_lo, int32_t t_hi, int32_t tb,
+                       int first_group, uint32_t* __restrict__ cursor, uint32_t* __restrict__ keys) {
+  const NetDev d = nets[net_idx];
+  const int64_t pairs = (d.k + 1) / 2;
+  const int64_t total = (int64_t)(t_hi - t_lo) * pairs;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(t_lo + q / pairs);
+    const uint32_t p = (uint32_t)(q % pairs);
+    const Draw2 dr = draw_pair(d, i, p);
+    const int64_t g = (int64_t)(i / tb) - first_group;
+    const uint32_t local = i - (uint32_t)((g + first_group) * tb);
+    const int64_t kbase = g * (int64_t)tb * d.k;  // keys of block g start here (all blocks but the last hold tb targets)
+    {
+      const uint32_t pos = atomicAdd(&cursor[g * d.n + dr.src[0]], 1u);
+      keys[kbase + pos] = (local << 16) | (2u * p);
+    }
+    if (2 * p + 1 < (uint32_t)d.k) {
+      const uint32_t pos = atomicAdd(&cursor[g * d.n + dr.src[1]], 1u);
+      keys[kbase + pos] = (local << 16) | (2u * p + 1u);
+    }
+  }
+}
+
+cudaError_t launch_build_fill_net(const NetDev* nets_dev, int net_idx, int32_t n, int first_group, int n_groups,
+                                  int32_t tb, uint32_t* cursor, uint32_t* keys, cudaStream_t s) {
+  const int32_t t_lo = first_group * tb;
+  const int32_t t_hi = min(n, (first_group + n_groups) * tb);
+  k_fill<<<152 * 8, 256, 0, s>>>(nets_dev, net_idx, t_lo, t_hi, tb, first_group, cursor, keys);
+  return cudaGetLastError();
+}
+
+// ---- finalize: sort each segment, write records and headers --------------------------------
+constexpr int kSegCap = 2048;  // keys sorted in shared memory per warp
+
+__global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ nets, const BlockWork* __restrict__ work,
+                                                  int net_idx, int first_group, int n_groups, int n_warps_blk,
+                                                  const uint32_t* __restrict__ cnt,
+                                                  const uint32_t* __restrict__ seg_end,
+                                                  const uint32_t* __restrict__ keys, void* __restrict__ rec_w,
+                                                  uint16_t* __restrict__ rec_tgt, uint8_t* __restrict__ rec_dly,
+                                                  uint4* __restrict__ hdr, int32_t* __restrict__ err,
+                                                  uint32_t* __restrict__ max_seg) {
+  extern __shared__ uint32_t sk[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t* buf = sk + wib * kSegCap;
+  const NetDev d = nets[net_idx];
+  const int64_t n_seg = (int64_t)n_groups * d.n;
+  const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t warp_stride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t sg = warp_global; sg < n_seg; sg += warp_stride) {
+    const int64_t g = sg / d.n;
+    const uint32_t src = (uint32_t)(sg % d.n);
+    const BlockWork w = work[d.first_block + first_group + g];
+    const uint32_t len = cnt[sg];
+    const uint32_t end = seg_end[sg];
+    const uint32_t start = end - len;
+    // keys of block g start at g * tb * K where tb = targets of a full block of this network
+    const int64_t key0 = g * (int64_t)work[d.first_block].nt * d.k + start;
+    if (len > kSegCap || len > 65535u) {
+      if (lane == 0) atomicOr(err, kErrSegment);
+      continue;
+    }
+    if (lane == 0 && len) atomicMax(max_seg, len);
+    uint32_t p2 = 32;
+    while (p2 < len) p2 <<= 1;
+    for (uint32_t q = lane; q < p2; q += 32) buf[q] = (q < len) ? keys[key0 + q] : 0xffffffffu;
+    __syncwarp();
+    // bitonic sort, ascending
+    for (uint32_t k = 2; k <= p2; k <<= 1) {
+      for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+        for (uint32_t q = lane; q < p2; q += 32) {
+          const uint32_t l = q ^ jj;
+          if (l > q) {
+            const uint32_t a = buf[q], b = buf[l];
+            const bool up = (q & k) == 0;
+            if ((a > b) == up) {
+              buf[q] = b;
+              buf[l] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // records
+    const int64_t r0 = w.rec_base + start;
+    for (uint32_t q = lane; q < len; q += 32) {
+      const uint32_t key = buf[q];
+      const uint32_t local = key >> 16, j = key & 0xffffu;
+      const Draw2 dr = draw_pair(d, (uint32_t)w.t0 + local, j >> 1);
+      const uint32_t s2 = dr.src[j & 1u], dl = dr.dly[j & 1u];
+      if (s2 != src) atomicOr(err, kErrBuild);
+      const float wv = (src < (uint32_t)d.n_exc) ? d.w_exc : d.w_inh;
+      if (d.wdtype == 1) reinterpret_cast<__nv_bfloat16*>(rec_w)[r0 + q] = __float2bfloat16_rn(wv);
+      else reinterpret_cast<float*>(rec_w)[r0 + q] = wv;
+      rec_tgt[r0 + q] = (uint16_t)local;
+      rec_dly[r0 + q] = (uint8_t)dl;
+    }
+    // header: base, then for warp w the number of entries with local target < (w + 1) * tw
+    uint32_t e_w = len;
+    if (lane < n_warps_blk) {
+      const uint32_t bound = min((uint32_t)((lane + 1) * w.tw), (uint32_t)w.nt);
+      uint32_t lo = 0, hi = len;  // first q with (buf[q] >> 16) >= bound
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((buf[mid] >> 16) < bound) lo = mid + 1;
+        else hi = mid;
+      }
+      e_w = lo;
+    }
+    uint32_t words[8];
+    words[0] = start;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const uint32_t a = __shfl_sync(0xffffffffu, e_w, 2 * q);
+      const uint32_t b = __shfl_sync(0xffffffffu, e_w, 2 * q + 1);
+      const uint32_t ea = (2 * q < n_warps_blk) ? a : len;
+      const uint32_t eb = (2 * q + 1 < n_warps_blk) ? b : len;
+      words[q + 1] = (ea & 0xffffu) | (eb << 16);
+    }
+    if (lane == 0) {
+      const int64_t h = w.hdr_base + src;
+      hdr[2 * h] = make_uint4(words[0], words[1], words[2], words[3]);
+      hdr[2 * h + 1] = make_uint4(words[4], words[5], words[6], words[7]);
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* work_dev, int net_idx, int first_group,
+                                      int n_groups, int n_warps_blk, const uint32_t* cnt, const uint32_t* seg_end,
+                                      const uint32_t* keys, void* rec_w, uint16_t* rec_tgt, uint8_t* rec_dly,
+                                      uint4* hdr, int32_t* err, uint32_t* max_seg, cudaStream_t s) {
+  const size_t smem = 8 * kSegCap * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_finalize<<<152 * 4, 256, smem, s>>>(nets_dev, work_dev, net_idx, first_group, n_groups, n_warps_blk, cnt,
+                                        seg_end, keys, rec_w, rec_tgt, rec_dly, hdr, err, max_seg);
+  return cudaGetLastError();
+}
+
+// ---- initial state ------------------------------------------------------------------------
+// V0 = V_reset + (V_th - V_reset) * ((u >> 8) 2^-24), u = word 0 of Philox(ctr = (i, 0, 2, 0));
+// each operation rounded to float.  I = 0, refractory counter = 0.
+__global__ void k_init_state(const NetDev* __restrict__ nets, int net_idx, float* __restrict__ V,
+                             float* __restrict__ I, int32_t* __restrict__ R) {
+  const NetDev d = nets[net_idx];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, kStreamV0, 0u), d.seed_lo, d.seed_hi);
+    const float frac = __fmul_rn((float)(r.x >> 8), 0x1p-24f);
+    const float span = __fsub_rn(d.v_th, d.v_reset);
+    V[d.neuron_base + i] = __fadd_rn(d.v_reset, __fmul_rn(span, frac));
+    I[d.neuron_base + i] = 0.0f;
+    R[d.neuron_base + i] = 0;
+  }
+}
+
+cudaError_t launch_init_state(const NetDev* net_host, const NetDev* net_dev, int net_idx, float* V, float* I,
+                              int32_t* R, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(4096, (net_host->n + 255) / 256);
+  k_init_state<<<max(blocks, 1), 256, 0, s>>>(net_dev, net_idx, V, I, R);
+  return cudaGetLastError();
+}
+
+// ---- Philox check kernel ---------------------------------------------------------------------
+__global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
+                         uint32_t* __restrict__ out) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4(ctr[4 * q], ctr[4 * q + 1], ctr[4 * q + 2], ctr[4 * q + 3]), key[2 * q],
+                                  key[2 * q + 1]);
+    out[4 * q] = r.x;
+    out[4 * q + 1] = r.y;
+    out[4 * q + 2] = r.z;
+    out[4 * q + 3] = r.w;
+  }
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(1024, (n + 255) / 256);
+  k_philox<<<max(blocks, 1), 256, 0, s>>>(ctr, key, n, out);
+  return cudaGetLastError();
+}
+
+// ---- export of the incoming synapses of a target range (connectivity checks) ------------------
+__global__ void k_export(const BlockWork* __restrict__ work, int block, const void* __restrict__ rec_w, int wdtype,
+                         const uint16_t* __restrict__ rec_tgt, const uint8_t* __restrict__ rec_dly,
+                         const uint4* __restrict__ hdr, int32_t n_src, int32_t t_begin, int32_t t_end,
+                         unsigned long long* counter, int32_t* o_src, int32_t* o_tgt, int32_t* o_dly, float* o_w,
+                         int64_t cap) {
+  const BlockWork w = work[block];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_src; s += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 h0 = hdr[2 * (w.hdr_base + s)];
+    const uint4 h1 = hdr[2 * (w.hdr_base + s) + 1];
+    const uint32_t words[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+    const uint32_t base = words[0];
+    // total entries = the last warp's end; all unused ends equal the total
+    const uint32_t len = words[7] >> 16;
+    for (uint32_t q = 0; q < len; ++q) {
+      const int64_t r = w.rec_base + base + q;
+      const int32_t tgt = w.t0 + rec_tgt[r];
+      if (tgt < t_begin || tgt >= t_end) continue;
+      const unsigned long long pos = atomicAdd(counter, 1ull);
+      if ((int64_t)pos >= cap) continue;
+      o_src[pos] = (int32_t)s;
+      o_tgt[pos] = tgt;
+      o_dly[pos] = rec_dly[r];
+      o_w[pos] = wdtype == 1 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(rec_w)[r])
+                             : reinterpret_cast<const float*>(rec_w)[r];
+    }
+  }
+}
+
+cudaError_t launch_export(const BlockWork* work_dev, int block, int32_t, const void* rec_w, int wdtype,
+                          const uint16_t* rec_tgt, const uint8_t* rec_dly, const uint4* hdr, int32_t n_src,
+                          int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src, int32_t* tgt,
+                          int32_t* dly, float* w, int64_t cap, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(1024, (n_src + 255) / 256);
+  k_export<<<max(blocks, 1), 256, 0, s>>>(work_dev, block, rec_w, wdtype, rec_tgt, rec_dly, hdr, n_src, t_begin, t_end,
+                                          counter, src, tgt, dly, w, cap);
+  return cudaGetLastError();
+}
+
+}  // namespace cortex

@@ -1,0 +1,218 @@
+// cortex_internal.cuh -- device-side data layout and helpers shared by the library's kernels.
+//
+// Layout in HBM (one handle, possibly many networks):
+//   records   SoA streams, one entry per synapse:  w (f32 or bf16), tgt (u16, target index local
+//             to its block), dly (u8, delay in steps).  Sorted by (block, source, target, draw):
+//             inside a block's sub-graph the synapses of one source are contiguous and ordered by
+//             target, so each warp's target sub-range is a contiguous piece of that segment.
+//   headers   one 32-byte header per (block, source):  u32 base (first record, relative to the
+//             block's record base) and u16 end[w] for the block's warps w = 0..n_w-1 (entries of
+//             warps 0..w); the segment of warp w is [base + end[w-1], base + end[w]).
+//   state     V (f32), I (f32), refractory counter (i32) per neuron.
+//   ring      per block [D][T_b] floats, D = d_max: cell (slot, j) holds the input due at the
+//             step t with t mod D == slot for local target j.
+//   pub       spike lists published per window: ids[(parity*W_max + ws) * n_total + pub_base + k],
+//             counts[(parity*W_max + ws) * n_blocks + block], flags[block] = windows completed.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace cortex {
+
+constexpr int kPoissonCap = 64;     // Poisson threshold table entries
+constexpr int kMaxWarps = 14;       // warps per block (32-byte header: 4 + 2 * 14 bytes)
+constexpr int kSpikeBatch = 32;     // spikes staged per delivery round
+
+constexpr uint32_t kStreamConn = 1u;
+constexpr uint32_t kStreamV0 = 2u;
+constexpr uint32_t kStreamPoisson = 3u;
+
+// device error word values
+constexpr int kErrTimeout = 1;
+constexpr int kErrRaster = 2;
+constexpr int kErrSegment = 4;
+constexpr int kErrBuild = 8;
+
+struct NetDev {
+  int32_t n, n_exc, n_inh, k_exc, k_inh, k;
+  int32_t d_min, d_max, depth, window;        // depth D = d_max, window W = d_min
+  uint32_t seed_lo, seed_hi;
+  int32_t wdtype;                              // 0 f32, 1 bf16
+  int32_t first_block, n_blocks;               // blocks of this network in the work table
+  int32_t n_ref, n_thr;
+  float p11, p21, p22;                         // FP32 propagators (from FP64 on the device)
+  float v_th, v_reset, j_ext;
+  float w_exc, w_inh;                          // stored weights (bf16-rounded when wdtype = 1)
+  // host-provided inputs for the propagator kernel
+  float tau_m, c_m, tau_syn, t_ref, dt, nu_ext_hz, j_exc_in, j_inh_in;
+  int64_t neuron_base;                         // offset of this network in V / I / R
+  int64_t raster_base, raster_cap;             // offset and capacity in the raster arrays
+  uint32_t thr[kPoissonCap];
+};
+
+struct BlockWork {
+  int32_t net;        // network index
+  int32_t group;      // block index within the network
+  int32_t t0;         // first target (network-local id)
+  int32_t nt;         // targets owned (T_b)
+  int32_t tw;         // targets per warp (T_w)
+  int32_t n_src;      // sources of the network (headers per block)
+  int64_t rec_base;   // first record of the block
+  int64_t hdr_base;   // first header of the block (in headers)
+  int64_t ring_base;  // first ring cell of the block (floats): D * T_b cells
+  int64_t pub_base;   // first publication slot of the block
+};
+
+struct StepArgs {
+  const NetDev* nets;
+  const BlockWork* work;
+  int32_t n_blocks;
+  int32_t w_max;                  // largest window over the networks
+  int64_t n_total;                // neurons over all networks (publication stride)
+  const void* rec_w;
+  const uint16_t* rec_tgt;
+  const uint8_t* rec_dly;
+  const uint4* hdr;               // 2 x uint4 per header
+  float* V;
+  float* I;
+  int32_t* R;
+  float* ring;
+  uint32_t* pub_ids;
+  uint32_t* pub_cnt;
+  uint32_t* pub_flag;
+  int32_t* raster_step;
+  int32_t* raster_id;
+  unsigned long long* raster_count;   // per network: spikes emitted so far
+  unsigned long long* events;         // per network: synaptic events so far
+  int32_t* err;
+  long long* step_counter;            // current step (device resident, graph friendly)
+  int32_t n_steps;                    // steps this launch
+  int32_t phases;                     // kPhaseUpdate | kPhaseDeliver
+  int32_t ring_smem;                  // 1: ring slice in shared memory
+  int32_t stage_bytes;                // shared staging capacity for record segments
+  int32_t max_nt, max_depth, max_nb;  // shared-memory layout maxima over the blocks
+  long long timeout_ns;
+  // delivery-only launches (cortex_deliver): fixed emission step
+  long long t_fixed;
+};
+
+constexpr int kPhaseUpdate = 1;
+constexpr int kPhaseDeliver = 2;
+constexpr int kPhaseBarrier = 4;    // persistent: grid barrier between the phases
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64 products with
+// the round multipliers, the high words xor-ed with the other counter words and the round key,
+// the key advanced by the Weyl constants after each round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = c.x, b = c.z;
+    const uint32_t lo0 = 0xD2511F53u * a, hi0 = __umulhi(0xD2511F53u, a);
+    const uint32_t lo1 = 0xCD9E8D57u * b, hi1 = __umulhi(0xCD9E8D57u, b);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// floor(u * n / 2^32): maps a uniform 32-bit word onto 0..n-1
+__device__ __forceinline__ uint32_t scale32(uint32_t u, uint32_t n) { return __umulhi(u, n); }
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// loads that bypass L1 (data written by other blocks during the same launch)
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) { return __ldcg(p); }
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---- mbarrier and bulk copy (TMA, non-tensor) ----------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+}  // namespace cortex
+
+// host launch wrappers (defined in build.cu and step.cu)
+namespace cortex {
+cudaError_t launch_props(NetDev* nets, int n_nets, cudaStream_t s);
+cudaError_t launch_build_count_net(const NetDev* nets_dev, int net_idx, int32_t n, int first_group, int n_groups,
+                                   int32_t tb, uint32_t* cnt, cudaStream_t s);
+cudaError_t launch_scan_groups(uint32_t* cnt, uint32_t* cursor, int n_groups, int32_t n_src, uint32_t* tmp,
+                               cudaStream_t s);
+cudaError_t launch_build_fill_net(const NetDev* nets_dev, int net_idx, int32_t n, int first_group, int n_groups,
+                                  int32_t tb, uint32_t* cursor, uint32_t* keys, cudaStream_t s);
+cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* work_dev, int net_idx, int first_group,
+                                      int n_groups, int n_warps_blk, const uint32_t* cnt, const uint32_t* seg_end,
+                                      const uint32_t* keys, void* rec_w, uint16_t* rec_tgt, uint8_t* rec_dly,
+                                      uint4* hdr, int32_t* err, uint32_t* max_seg, cudaStream_t s);
+cudaError_t launch_init_state(const NetDev* net_host, const NetDev* net_dev, int net_idx, float* V, float* I,
+                              int32_t* R, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, cudaStream_t s);
+cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s);
+cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s);
+size_t step_smem_bytes(int max_nt, int max_depth, int w_max, int max_nb, bool ring_smem, int stage_bytes);
+cudaError_t step_kernel_attributes(size_t smem);
+int step_occupancy(int threads, size_t smem);
+cudaError_t launch_export(const BlockWork* work_dev, int block, int32_t t0_net, const void* rec_w, int wdtype,
+                          const uint16_t* rec_tgt, const uint8_t* rec_dly, const uint4* hdr, int32_t n_src,
+                          int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src, int32_t* tgt,
+                          int32_t* dly, float* w, int64_t cap, cudaStream_t s);
+}  // namespace cortex

@@ -1,0 +1,190 @@
+"""GPU path vs the oracle, through the C ABI.
+
+Bit-exact: Philox words, FP32 propagators and Poisson thresholds, initial potentials, the
+connectivity (multiset of (source, target, delay, weight)), and -- in FP32 with the summation
+order (emission step, source, draw) on both sides -- the whole spike raster and final state."""
+import numpy as np
+import pytest
+
+from helpers import first_mismatch, oracle_params, oracle_run
+from oracle import oracle as orc
+from paper_2406_03762_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C0 = W.CONFIGS["c0"]
+
+
+def _kat():
+    import os
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            w = [int(x, 16) for x in line.split()]
+            rows.append(w)
+    return np.array(rows, dtype=np.uint64).astype(np.uint32)
+
+
+def test_philox_device_known_answers(cortex):
+    k = _kat()
+    out = cortex.philox(k[:, 0:4], k[:, 4:6])
+    assert np.array_equal(out, k[:, 6:10])
+
+
+def test_philox_device_matches_oracle(cortex):
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2**32, size=(500, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(500, 2), dtype=np.uint64).astype(np.uint32)
+    out = cortex.philox(ctr, key)
+    for q in range(0, 500, 7):
+        assert np.array_equal(out[q], orc.philox4x32_10(ctr[q], key[q]))
+
+
+SPECS = [C0["spec"], W.NetSpec(4000, 1000, 400, 100, d_min=5, d_max=40, nu_ext_hz=12000.0),
+         W.NetSpec(800, 200, 900, 225, weight_dtype=W.BF16), W.brunel(3000, 300, nu_ext_hz=17321.5)]
+
+
+@pytest.mark.parametrize("spec", SPECS)
+def test_constants_bit_equal(cortex, spec):
+    with cortex.Network(spec, 1) as net:
+        c6, thr, nref = net.constants()
+    ref = orc.Network(oracle_params(spec), 1)
+    c8, othr, onref = ref.constants_f32()
+    assert c6[0] == c8[0] and c6[1] == c8[1] and c6[2] == c8[2]          # P11, P21, P22
+    assert c6[3] == c8[4] and c6[4] == c8[5] and c6[5] == c8[6]          # weights, J_ext
+    assert np.array_equal(thr, othr) and nref == onref
+
+
+def test_initial_state_bit_equal(cortex):
+    spec, seed = C0["spec"], C0["seed"]
+    with cortex.Network(spec, seed) as net:
+        v, i, r = net.state()
+    ov, oi, orr = orc.Network(oracle_params(spec), seed).state()
+    assert np.array_equal(v.astype(np.float64), ov)
+    assert np.all(i == 0) and np.all(r == 0)
+
+
+def _oracle_incoming(spec, seed, t_begin, t_end):
+    p = oracle_params(spec)
+    ref = orc.Network(p, seed)
+    row, tgt, dly = ref.outgoing()
+    src = np.repeat(np.arange(len(row) - 1), np.diff(row)).astype(np.int64)
+    keep = (tgt >= t_begin) & (tgt < t_end)
+    rec = np.stack([tgt[keep], src[keep], dly[keep]], axis=1)
+    order = np.lexsort((rec[:, 2], rec[:, 1], rec[:, 0]))
+    return rec[order], ref
+
+
+@pytest.mark.parametrize("spec,warps", [(C0["spec"], 8), (SPECS[1], 4), (SPECS[2], 14)])
+def test_connectivity_bit_exact(cortex, spec, warps):
+    seed = 77
+    n = spec.n
+    with cortex.Network(spec, seed, cortex.make_options(warps_per_block=warps)) as net:
+        s, t, d, w = net.export_synapses(0, n)
+        c6, _, _ = net.constants()
+    want, _ = _oracle_incoming(spec, seed, 0, n)
+    got = np.stack([t, s, d], axis=1).astype(np.int64)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+    exp_w = np.where(s < spec.n_exc, c6[3], c6[4]).astype(np.float32)
+    assert np.array_equal(w, exp_w)
+    # in-degree exactly K_E / K_I for every target
+    assert np.all(np.bincount(t[s < spec.n_exc], minlength=n) == spec.k_exc)
+    assert np.all(np.bincount(t[s >= spec.n_exc], minlength=n) == spec.k_inh)
+
+
+MODES = [
+    dict(),                                            # persistent, automatic ring placement
+    dict(ring=2),                                      # persistent, ring in global memory
+    dict(mode=1),                                      # split update / delivery launches
+    dict(warps_per_block=4, steps_per_launch=97),      # other warp split, odd launch chunks
+    dict(warps_per_block=14, use_graph=-1),
+]
+
+
+@pytest.mark.parametrize("opts", MODES)
+def test_raster_c0_bit_exact(cortex, opts):
+    spec, seed, steps = C0["spec"], C0["seed"], C0["steps"]
+    with cortex.Network(spec, seed, cortex.make_options(**opts)) as net:
+        net.simulate(steps)
+        gs, gi = net.spikes()
+        gv, gc, gr = net.state()
+        st = net.stats()
+    ref, os_, oi, _ = oracle_run(spec, seed, steps)
+    assert first_mismatch(gs, gi, os_, oi) == -1, f"first mismatch at spike {first_mismatch(gs, gi, os_, oi)}"
+    ov, oc, orr = ref.state()
+    assert np.array_equal(gv.astype(np.float64), ov)
+    assert np.array_equal(gc.astype(np.float64), oc)
+    assert np.array_equal(gr, orr)
+    assert st["events"] == ref.events
+    assert st["spikes"] == len(os_)
+
+
+def test_raster_deep_delays_window(cortex):
+    """d = 5..40: five steps per barrier window, ring depth 40."""
+    spec, seed, steps = SPECS[1], 2024, 1500
+    for opts in (dict(), dict(mode=1)):
+        with cortex.Network(spec, seed, cortex.make_options(**opts)) as net:
+            net.simulate(steps)
+            gs, gi = net.spikes()
+            gv, _, _ = net.state()
+        ref, os_, oi, _ = oracle_run(spec, seed, steps)
+        assert len(os_) > 1000
+        assert first_mismatch(gs, gi, os_, oi) == -1
+        assert np.array_equal(gv.astype(np.float64), ref.state()[0])
+
+
+def test_simulate_in_pieces_equals_one_call(cortex):
+    spec, seed = C0["spec"], C0["seed"]
+    with cortex.Network(spec, seed) as a, cortex.Network(spec, seed, cortex.make_options(steps_per_launch=50)) as b:
+        a.simulate(700)
+        for n in (1, 2, 97, 300, 300):
+            b.simulate(n)
+        for x, y in zip(a.spikes(), b.spikes()):
+            assert np.array_equal(x, y)
+        for x, y in zip(a.state(), b.state()):
+            assert np.array_equal(x, y)
+
+
+def test_bf16_weights_match_oracle_with_bf16_weights(cortex):
+    """BF16 storage with FP32 accumulation is deterministic: equal to the FP32 oracle run with the
+    weights rounded to bfloat16 (J_E 87.8 -> 88, J_I -439 -> -440)."""
+    spec, seed, steps = SPECS[2], 99, 1500
+    with cortex.Network(spec, seed) as net:
+        net.simulate(steps)
+        gs, gi = net.spikes()
+        c6, _, _ = net.constants()
+    assert c6[3] == 88.0 and c6[4] == -440.0
+    ref, os_, oi, _ = oracle_run(spec, seed, steps)
+    assert len(os_) > 100
+    assert first_mismatch(gs, gi, os_, oi) == -1
+
+
+def test_batch_every_instance_matches_oracle(cortex):
+    specs, seeds = W.small_batch_specs()
+    steps = 800
+    with cortex.Network(specs, seeds) as net:
+        net.simulate(steps)
+        res = [net.spikes(b) for b in range(len(specs))]
+        st = net.stats()
+    assert st["n_nets"] == len(specs)
+    total = 0
+    for b, (spec, seed) in enumerate(zip(specs, seeds)):
+        ref, os_, oi, _ = oracle_run(spec, seed, steps)
+        gs, gi = res[b]
+        assert first_mismatch(gs, gi, os_, oi) == -1, f"network {b}"
+        total += ref.events
+    assert st["events"] == total
+
+
+def test_deliver_counts_out_degree(cortex):
+    spec, seed = W.NetSpec(8000, 2000, 800, 200), 5
+    rng = np.random.default_rng(1)
+    ids = np.unique(rng.integers(0, spec.n, 300))
+    with cortex.Network(spec, seed) as net:
+        src, tgt, dly, w = net.export_synapses(0, spec.n)
+        ms, ev = net.deliver(ids, t_emit=0, reps=1)
+    outdeg = np.bincount(src, minlength=spec.n)
+    assert ev == int(outdeg[ids].sum())
+    assert ms > 0
