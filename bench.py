@@ -1,0 +1,362 @@
+"""Benchmark: synaptic events/s and real-time factor of the spike-delivery hot path on one GB300.
+
+One benchmark step = one cortex_simulate call of --sim-steps simulation steps (default 1000 steps =
+100 ms of simulated time) of the balanced random network N = 112,500, K = 11,250, FP32 weights
+(1.27e9 synapses, about 9.4 GB on the device, so every step reads far more than the 129 MB L2).
+Each simulation step runs the whole hot path: neuron update, spike compaction, publication, grid
+barrier and delivery.  Inputs are synthetic (a seeded network), built on the device before timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank simulates its own replica (weak scaling, no collective on the data
+path); rank 0 prints one JSON line.  --impl reference times the CPU oracle on the host cores
+(bounded sample of the same network) and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "synaptic events/s"
+UNIT = "events/s"
+BYTES_PER_EVENT = {0: 7, 1: 5}   # FP32: w 4 B + local target 2 B + delay 1 B; BF16: 2 + 2 + 1
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle runs (separate spawned process: started before any CUDA call)
+# ---------------------------------------------------------------------------------------------
+def _oracle_job(cfg_name: str, sample_steps: int, n_samples: int, q):
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    from paper_2406_03762_gb300 import workloads as W
+    cfg = W.CONFIGS[cfg_name] if cfg_name in W.CONFIGS else W.PROFILE[cfg_name]
+    spec = cfg["spec"]
+    d = {k: v for k, v in spec.as_dict().items() if k in orc.Params.__dataclass_fields__}
+    d["bf16_weights"] = int(spec.weight_dtype == 1)
+    t0 = time.perf_counter()
+    net = orc.Network(orc.Params(**d), cfg["seed"])
+    build_s = time.perf_counter() - t0
+    out = []
+    for _ in range(n_samples):
+        e0 = net.events
+        t0 = time.perf_counter()
+        net.simulate(sample_steps)
+        out.append((net.events - e0, time.perf_counter() - t0))
+    q.put(dict(build_s=build_s, samples=out, step=net.step))
+
+
+def start_oracle(cfg_name, sample_steps, n_samples):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_job, args=(cfg_name, sample_steps, n_samples, q), daemon=True)
+    p.start()
+    return p, q
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"cortex_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+def reference_arm(args):
+    """The oracle on the host cores, bounded samples of the same network."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = _config(args.config)
+    p, q = start_oracle(args.config, args.ref_sample_steps, args.warmup + args.steps)
+    res = q.get()
+    p.join(timeout=30)
+    timed = res["samples"][args.warmup:]
+    ev = sum(e for e, _ in timed)
+    sec = sum(s for _, s in timed)
+    value = ev / sec if sec > 0 else 0.0
+    spec = cfg["spec"]
+    sim_s = args.ref_sample_steps * spec.dt * 1e-3 * len(timed)
+    sample = (f"{cfg['name']}: oracle build {res['build_s']:.1f} s (untimed), then {args.warmup} + {args.steps} "
+              f"samples of {args.ref_sample_steps} simulation steps each, single-threaded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(1, len(timed)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_neurons": spec.n, "k": spec.k, "sim_steps_per_step": args.ref_sample_steps},
+        "rtf": sec / sim_s if sim_s > 0 else None,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def our_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    want_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
+    oracle_proc = start_oracle(args.config, args.cpu_sample_steps, 1) if want_cpu else None
+
+    import torch
+    from paper_2406_03762_gb300 import cortex
+    from paper_2406_03762_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cortex.load()
+    cfg = _config(args.config)
+    spec = cfg["spec"]
+    stream = torch.cuda.Stream()
+    opts = cortex.make_options(steps_per_launch=args.steps_per_launch, warps_per_block=args.warps)
+    net = cortex.Network(spec, cfg["seed"] + 1000 * rank, opts, stream=stream)
+    st0 = net.stats()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        net.simulate(args.sim_steps)
+    net.clear_spikes()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev_a = torch.cuda.Event(enable_timing=True)
+    ev_b = torch.cuda.Event(enable_timing=True)
+    e_before = net.stats()["events"]
+    ev_a.record(stream)
+    kern_ms = 0.0
+    for _ in range(args.steps):
+        net.simulate(args.sim_steps)          # launches on `stream`
+        kern_ms += net.stats()["simulate_ms"]
+    ev_b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev_a.elapsed_time(ev_b)
+    st = net.stats()
+    events = st["events"] - e_before
+    spikes = st["spikes"]
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    e = torch.tensor([float(events)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    events_all = float(e.item())
+    value = events_all / (ms_max * 1e-3)
+    sim_s = args.steps * args.sim_steps * spec.dt * 1e-3
+    rtf = (ms_max * 1e-3) / sim_s
+
+    # end to end through the public API: simulate, then read the step's spikes back to the host
+    net.clear_spikes()
+    e0 = net.stats()["events"]
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        net.simulate(args.sim_steps)
+        s_, i_ = net.spikes()
+        d2h += s_.nbytes + i_.nbytes
+        net.clear_spikes()
+    e2e_s = time.perf_counter() - t0
+    e2e_events = net.stats()["events"] - e0
+    e2e_value = e2e_events * world / e2e_s
+
+    # roofline of the dominant kernel (the persistent step kernel): algorithmic record bytes
+    launches_per_step = max(1, -(-args.sim_steps // args.steps_per_launch))
+    launches = args.steps * launches_per_step
+    bpe = BYTES_PER_EVENT[spec.weight_dtype]
+    per_launch_bytes = events * bpe / launches
+    launch_ms = kern_ms / launches
+    peak, peak_kind = _peaks()
+    achieved = per_launch_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = _traffic(per_launch_bytes / bpe, spec)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if spec.weight_dtype == 0 else "bf16", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_neurons": spec.n, "k": spec.k, "synapses": st0["n_synapses"],
+                   "sim_steps_per_step": args.sim_steps, "dt_ms": spec.dt, "replicas": world,
+                   "l2": "inputs larger than L2 (network %.1f GB)" % (st0["device_bytes"] / 1e9),
+                   "blocks": st0["n_blocks"], "threads_per_block": st0["threads_per_block"],
+                   "ring_in_smem": st0["ring_in_smem"]},
+        "rtf": rtf,
+        "spikes": spikes, "events": events,
+        "build_ms": st0["build_ms"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind, "bytes_per_event": bpe,
+                     "kernel": "k_step (persistent)", "launch_ms": launch_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if oracle_proc is not None:
+        p, q = oracle_proc
+        try:
+            res = q.get(timeout=args.cpu_timeout)
+            ev_c, sec_c = res["samples"][0]
+            line["cpu_baseline"] = {
+                "value": ev_c / sec_c, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{cfg['name']}: first {args.cpu_sample_steps} simulation steps after an untimed oracle "
+                          f"build ({res['build_s']:.0f} s), single-threaded"}
+        except Exception as ex:  # noqa: BLE001
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"not finished: {type(ex).__name__}"}
+        p.join(timeout=5)
+        if p.is_alive():
+            p.terminate()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _traffic(events_per_launch, spec):
+    """DRAM bytes per launch from the committed ncu summary, scaled by events, if the kernel
+    source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        import hashlib
+        h = hashlib.sha256()
+        for name in ("step.cu", "cortex_internal.cuh"):
+            with open(os.path.join(ROOT, "paper_2406_03762_gb300", "csrc", name), "rb") as g:
+                h.update(g.read())
+        if d.get("source_sha256") != h.hexdigest():
+            return None
+        return d["dram_bytes_per_event"] * events_per_launch
+    except Exception:
+        return None
+
+
+def deliver_arm(args):
+    """Delivery kernel alone (split phase) on a fixed set of spiking sources: the kernel whose bytes
+    per launch are large enough to measure against the HBM roofline."""
+    import numpy as np
+    import torch
+    from paper_2406_03762_gb300 import cortex
+    from paper_2406_03762_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cortex.load()
+    cfg = _config(args.config)
+    spec = cfg["spec"]
+    net = cortex.Network(spec, cfg["seed"], cortex.make_options(warps_per_block=args.warps), stream=torch.cuda.Stream())
+    rng = np.random.default_rng(1)
+    ids = np.unique(rng.choice(spec.n, size=min(args.spikes, spec.n), replace=False))
+    for _ in range(args.warmup):
+        net.deliver(ids, t_emit=0, reps=1)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms, ev = net.deliver(ids, t_emit=0, reps=args.steps)
+    clk = clocks.stop()
+    bpe = BYTES_PER_EVENT[spec.weight_dtype]
+    peak, peak_kind = _peaks()
+    achieved = ev * bpe / (ms * 1e-3) / 1e9
+    line = {"metric": "delivery events/s", "value": ev / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "config": {"workload": cfg["name"], "spikes_per_launch": int(len(ids)), "events_per_launch": ev},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (delivery phase)"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
+def _config(name):
+    from paper_2406_03762_gb300 import workloads as W
+    if name in W.CONFIGS:
+        return W.CONFIGS[name]
+    return W.PROFILE[name]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c1")
+    ap.add_argument("--sim-steps", type=int, default=1000)
+    ap.add_argument("--steps-per-launch", type=int, default=1000)
+    ap.add_argument("--cpu-sample-steps", type=int, default=1500)
+    ap.add_argument("--cpu-timeout", type=float, default=900.0)
+    ap.add_argument("--ref-sample-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="simulate", choices=["simulate", "deliver"])
+    ap.add_argument("--spikes", type=int, default=10000)
+    ap.add_argument("--warps", type=int, default=0, help="warps per block (0: library default)")
+    args = ap.parse_args()
+    if args.mode == "deliver":
+        return deliver_arm(args)
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/cortex.h"
+#include "cortex.h"
 #include "cortex_internal.cuh"
 
 using namespace cortex;
@@ -50,16 +50,16 @@ struct cortex_net {
   int64_t n_total = 0, total_syn = 0, total_ring = 0, total_hdr = 0, total_raster = 0;
   // device arrays
   void* rec_w = nullptr;
-  uint16_t* rec_tgt = nullptr;
-  uint8_t* rec_dly = nullptr;
+  uint16_t* rec_meta = nullptr;
   uint4* hdr = nullptr;
+  unsigned long long* row_base = nullptr;
   float* V = nullptr;
   float* I = nullptr;
   int32_t* R = nullptr;
   float* ring = nullptr;
   uint32_t* pub_ids = nullptr;
   uint32_t* pub_cnt = nullptr;
-  uint32_t* pub_flag = nullptr;
+  unsigned long long* pub_flag = nullptr;
   int32_t* raster_step = nullptr;
   int32_t* raster_id = nullptr;
   unsigned long long* raster_count = nullptr;
@@ -70,11 +70,11 @@ struct cortex_net {
   std::vector<void*> allocs;
   size_t device_bytes = 0;
   // plan
-  int n_warps = 8, threads = 256, n_blocks = 0, n_sm = 0;
+  int n_warps = 14, threads = 448, n_blocks = 0, n_sm = 0;
   int w_max = 1, w_split = 1, max_nt = 0, max_depth = 0, max_nb = 0;
   bool ring_smem = false;
   int mode = CORTEX_MODE_PERSISTENT;
-  int stage_bytes = 0;
+  int stage_bytes = 0, batch = 32, cap_w = 0, cap_m = 0;
   size_t smem = 0;
   int steps_per_launch = 1000;
   bool use_graph = true;
@@ -178,9 +178,9 @@ StepArgs make_args(cortex_net* h) {
   a.w_max = h->w_max;
   a.n_total = h->n_total;
   a.rec_w = h->rec_w;
-  a.rec_tgt = h->rec_tgt;
-  a.rec_dly = h->rec_dly;
+  a.rec_meta = h->rec_meta;
   a.hdr = h->hdr;
+  a.row_base = h->row_base;
   a.V = h->V;
   a.I = h->I;
   a.R = h->R;
@@ -195,6 +195,9 @@ StepArgs make_args(cortex_net* h) {
   a.err = h->err;
   a.step_counter = h->step_counter;
   a.stage_bytes = h->stage_bytes;
+  a.batch = h->batch;
+  a.cap_w = h->cap_w;
+  a.cap_m = h->cap_m;
   a.max_nt = h->max_nt;
   a.max_depth = h->max_depth;
   a.max_nb = h->max_nb;
@@ -219,6 +222,7 @@ cudaError_t launch_split_window(cortex_net* h, int wn, cudaStream_t s) {
   cudaError_t e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s);
   if (e != cudaSuccess) return e;
   a.phases = kPhaseDeliver;
+  a.ring_smem = h->ring_smem ? 1 : 0;  // the delivery launch stages its ring slice in shared memory
   e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s);
   if (e != cudaSuccess) return e;
   return launch_advance_split(a, h->n_nets, wn, s);
@@ -271,57 +275,66 @@ int build_network(cortex_net* h, int b, const std::vector<int32_t>& tb) {
   const NetDev& nd = h->nets_h[b];
   const int64_t n = nd.n;
   const int nbk = nd.n_blocks;
-  // waves of blocks bounded by the key budget
+  cudaStream_t st = h->stream;
+  // 1. counts of every (block, source) and the rows of the CSR by source
+  uint32_t *cnt_all = nullptr, *off_all = nullptr, *rowcnt = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&cnt_all, (size_t)nbk * n * 4, st));
+  CUDA_TRY(cudaMallocAsync((void**)&off_all, (size_t)nbk * n * 4, st));
+  CUDA_TRY(cudaMallocAsync((void**)&rowcnt, (size_t)n * 4, st));
+  CUDA_TRY(cudaMemsetAsync(cnt_all, 0, (size_t)nbk * n * 4, st));
+  CUDA_TRY(launch_build_count_net(h->nets_d, b, (int32_t)n, 0, nbk, tb[b], cnt_all, st));
+  CUDA_TRY(launch_build_rows(cnt_all, nbk, (int32_t)n, off_all, rowcnt, h->row_base + nd.row_off, st));
+  // 2. waves of blocks (keys scratch bounded): scan, fill, finalize
   const int64_t keys_per_block = (int64_t)tb[b] * nd.k;
   int per_wave = (int)std::max<int64_t>(1, std::min<int64_t>(nbk, (int64_t)(kKeyBudget / 4) / std::max<int64_t>(1, keys_per_block)));
-  // counters: 2 x per_wave x n words
-  while (per_wave > 1 && (size_t)per_wave * n * 8 > kKeyBudget) per_wave /= 2;
-  uint32_t *cnt = nullptr, *cursor = nullptr, *keys = nullptr;
-  CUDA_TRY(cudaMallocAsync((void**)&cnt, (size_t)per_wave * n * 4, h->stream));
-  CUDA_TRY(cudaMallocAsync((void**)&cursor, (size_t)per_wave * n * 4, h->stream));
-  CUDA_TRY(cudaMallocAsync((void**)&keys, (size_t)std::max<int64_t>(1, per_wave * keys_per_block) * 4, h->stream));
+  uint32_t *cursor = nullptr, *keys = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&cursor, (size_t)per_wave * n * 4, st));
+  CUDA_TRY(cudaMallocAsync((void**)&keys, (size_t)std::max<int64_t>(1, per_wave * keys_per_block) * 4, st));
   int rc = CORTEX_OK;
   for (int g0 = 0; g0 < nbk && rc == CORTEX_OK; g0 += per_wave) {
     const int ng = std::min(per_wave, nbk - g0);
-    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)ng * n * 4, h->stream);
-    if (e == cudaSuccess) e = launch_build_count_net(h->nets_d, b, (int32_t)n, g0, ng, tb[b], cnt, h->stream);
-    if (e == cudaSuccess) e = launch_scan_groups(cnt, cursor, ng, (int32_t)n, nullptr, h->stream);
-    if (e == cudaSuccess) e = launch_build_fill_net(h->nets_d, b, (int32_t)n, g0, ng, tb[b], cursor, keys, h->stream);
+    uint32_t* cnt = cnt_all + (size_t)g0 * n;
+    cudaError_t e = launch_scan_groups(cnt, cursor, ng, (int32_t)n, nullptr, st);
+    if (e == cudaSuccess) e = launch_build_fill_net(h->nets_d, b, (int32_t)n, g0, ng, tb[b], cursor, keys, st);
     if (e == cudaSuccess)
-      e = launch_build_finalize_net(h->nets_d, h->work_d, b, g0, ng, h->n_warps, cnt, cursor, keys, h->rec_w,
-                                    h->rec_tgt, h->rec_dly, h->hdr, h->err, h->max_seg, h->stream);
+      e = launch_build_finalize_net(h->nets_d, h->work_d, b, g0, ng, h->n_warps, cnt, cursor, keys, off_all,
+                                    h->row_base, h->rec_w, h->rec_meta, h->hdr, h->err, h->max_seg, st);
     if (e != cudaSuccess) rc = fail(CORTEX_ERR_CUDA, std::string("builder: ") + cudaGetErrorString(e));
   }
-  cudaFreeAsync(cnt, h->stream);
-  cudaFreeAsync(cursor, h->stream);
-  cudaFreeAsync(keys, h->stream);
+  cudaFreeAsync(cnt_all, st);
+  cudaFreeAsync(off_all, st);
+  cudaFreeAsync(rowcnt, st);
+  cudaFreeAsync(cursor, st);
+  cudaFreeAsync(keys, st);
   return rc;
 }
 
 int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   cudaDeviceProp prop;
   CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
-  const int smem_cap = (int)prop.sharedMemPerBlockOptin - 1024;  // leave room for static shared memory
+  const size_t smem_cap = (size_t)prop.sharedMemPerBlockOptin - 1024;  // room for static shared memory
   const int wsz = h->wdtype == CORTEX_BF16 ? 2 : 4;
-  const int need_stage = (int)h->max_seg_len * (wsz + 3) + 3 * 32 + 64;
-  const int want_stage = std::max(need_stage, 48 * 1024);
+  step_staging_caps((int)std::max<uint32_t>(h->max_seg_len, 1u), wsz, &h->cap_w, &h->cap_m);
+  const size_t per_spike = (size_t)kStages * (h->cap_w + h->cap_m);  // staging bytes per spike of a round
   const size_t base = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, false, 0);
   const size_t ring_bytes = (size_t)h->max_depth * h->max_nt * 4;
+  auto batch_for = [&](size_t fixed) -> int {
+    if (fixed >= smem_cap) return 0;
+    return (int)std::min<size_t>(kSpikeBatch, (smem_cap - fixed) / per_spike);
+  };
   bool smem_ring;
   if (o.ring == CORTEX_RING_SMEM) smem_ring = true;
   else if (o.ring == CORTEX_RING_GLOBAL) smem_ring = false;
-  else smem_ring = base + ring_bytes + (size_t)want_stage <= (size_t)smem_cap;
-  if (h->mode == CORTEX_MODE_SPLIT) smem_ring = false;
-  const size_t fixed = base + (smem_ring ? ring_bytes : 0);
-  if (fixed + (size_t)need_stage > (size_t)smem_cap)
+  else smem_ring = batch_for(base + ring_bytes) >= 16;
+  const int b = batch_for(base + (smem_ring ? ring_bytes : 0));
+  if (b < 1)
     return fail(CORTEX_ERR_UNSUPPORTED, "shared memory too small for this plan (ring " + std::to_string(ring_bytes) +
-                                            " B, state " + std::to_string(base) + " B, staging " +
-                                            std::to_string(need_stage) + " B)");
-  int stage = (int)std::min<size_t>((size_t)smem_cap - fixed, 96 * 1024);
-  stage = std::max(stage, need_stage) & ~127;
+                                            " B, state " + std::to_string(base) + " B, staging per spike " +
+                                            std::to_string(per_spike) + " B)");
   h->ring_smem = smem_ring;
-  h->stage_bytes = stage;
-  h->smem = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, smem_ring, stage);
+  h->batch = b;
+  h->stage_bytes = (int)(per_spike * b);
+  h->smem = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, smem_ring, h->stage_bytes);
   CUDA_TRY(step_kernel_attributes(h->smem));
   return CORTEX_OK;
 }
@@ -386,7 +399,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   h->params.assign(params, params + n_nets);
   h->seeds.assign(seeds, seeds + n_nets);
   h->wdtype = params[0].weight_dtype;
-  h->n_warps = o.warps_per_block ? o.warps_per_block : 8;
+  h->n_warps = o.warps_per_block ? o.warps_per_block : 14;
   h->threads = 32 * h->n_warps;
   h->mode = o.mode;
   h->steps_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 1000;
@@ -415,6 +428,8 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     d.d_max = p.d_max;
     d.depth = p.d_max;
     d.window = p.d_min;
+    d.dbits = 0;
+    while ((1 << d.dbits) < p.d_max - p.d_min + 1) ++d.dbits;
     d.seed_lo = (uint32_t)seeds[b];
     d.seed_hi = (uint32_t)(seeds[b] >> 32);
     d.wdtype = p.weight_dtype;
@@ -430,6 +445,9 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     d.j_exc_in = p.j_exc;
     d.j_inh_in = p.j_inh;
     d.neuron_base = neuron_base;
+    d.row_off = neuron_base;
+    d.rec_base = rec;
+    d.hdr_base = hdr;
     const int nbk = (int)ceil_div(d.n, tb[b]);
     d.first_block = (int)h->work_h.size();
     d.n_blocks = nbk;
@@ -437,7 +455,11 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     d.raster_base = raster;
     d.raster_cap = rcap;
     raster += rcap;
-    const int32_t tw = (int32_t)ceil_div(tb[b], h->n_warps);
+    const int32_t tw = (int32_t)ceil_div(tb[b], h->n_warps);  // targets per warp
+    if ((int64_t)tw > (1ll << (16 - d.dbits)))
+      return bail(fail(CORTEX_ERR_UNSUPPORTED, "targets per delivery warp (" + std::to_string(tw) +
+                                                   ") do not fit the 16-bit record with " + std::to_string(d.dbits) +
+                                                   " delay bits; use more warps per block"));
     for (int g = 0; g < nbk; ++g) {
       BlockWork w;
       memset(&w, 0, sizeof(w));
@@ -489,16 +511,16 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(h->alloc(&h->nets_d, sizeof(NetDev) * n_nets), "alloc nets");
   TRY(h->alloc(&h->work_d, sizeof(BlockWork) * h->n_blocks), "alloc work");
   TRY(h->alloc(&h->rec_w, wsz * h->total_syn + 64), "alloc weights");
-  TRY(h->alloc(&h->rec_tgt, 2 * h->total_syn + 64), "alloc targets");
-  TRY(h->alloc(&h->rec_dly, h->total_syn + 64), "alloc delays");
+  TRY(h->alloc(&h->rec_meta, 2 * h->total_syn + 64), "alloc record meta");
   TRY(h->alloc(&h->hdr, 32 * h->total_hdr), "alloc headers");
+  TRY(h->alloc(&h->row_base, 8 * h->n_total), "alloc rows");
   TRY(h->alloc(&h->V, 4 * h->n_total), "alloc V");
   TRY(h->alloc(&h->I, 4 * h->n_total), "alloc I");
   TRY(h->alloc(&h->R, 4 * h->n_total), "alloc R");
   TRY(h->alloc(&h->ring, 4 * h->total_ring), "alloc ring");
   TRY(h->alloc(&h->pub_ids, 4 * (size_t)2 * h->w_max * h->n_total), "alloc spike lists");
   TRY(h->alloc(&h->pub_cnt, 4 * (size_t)2 * h->w_max * h->n_blocks), "alloc spike counts");
-  TRY(h->alloc(&h->pub_flag, 4 * (size_t)h->n_blocks), "alloc flags");
+  TRY(h->alloc(&h->pub_flag, 8 * (size_t)h->n_blocks), "alloc flags");
   TRY(h->alloc(&h->raster_step, 4 * h->total_raster), "alloc raster");
   TRY(h->alloc(&h->raster_id, 4 * h->total_raster), "alloc raster");
   TRY(h->alloc(&h->raster_count, 8 * (size_t)n_nets), "alloc counters");
@@ -525,7 +547,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     TRY(launch_init_state(&h->nets_h[b], h->nets_d, b, h->V, h->I, h->R, s), "init state");
   }
   TRY(cudaMemsetAsync(h->ring, 0, 4 * h->total_ring, s), "memset ring");
-  TRY(cudaMemsetAsync(h->pub_flag, 0, 4 * (size_t)h->n_blocks, s), "memset flags");
+  TRY(cudaMemsetAsync(h->pub_flag, 0, 8 * (size_t)h->n_blocks, s), "memset flags");
   TRY(cudaMemsetAsync(h->pub_cnt, 0, 4 * (size_t)2 * h->w_max * h->n_blocks, s), "memset counts");
   TRY(cudaMemsetAsync(h->raster_count, 0, 8 * (size_t)n_nets, s), "memset");
   TRY(cudaMemsetAsync(h->events, 0, 8 * (size_t)n_nets, s), "memset");
@@ -540,7 +562,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   rc = choose_stage_and_ring(h, o);
   if (rc != CORTEX_OK) return bail(rc);
   if (h->mode == CORTEX_MODE_PERSISTENT) {
-    const int occ = step_occupancy(h->threads, h->smem);
+    const int occ = step_occupancy(h->threads, h->smem, h->ring_smem);
     if (occ * h->n_sm < h->n_blocks) {
       if (o.mode == CORTEX_MODE_PERSISTENT && opts && opts->mode == CORTEX_MODE_PERSISTENT && o.ring == CORTEX_RING_SMEM)
         return bail(fail(CORTEX_ERR_UNSUPPORTED, "blocks cannot all be resident for the persistent kernel"));
@@ -717,8 +739,8 @@ int cortex_export_synapses(cortex_net* h, int32_t net_idx, int32_t t_begin, int3
   for (int g = 0; g < d.n_blocks; ++g) {
     const BlockWork& w = h->work_h[d.first_block + g];
     if (w.t0 + w.nt <= t_begin || w.t0 >= t_end) continue;
-    CUDA_TRY(launch_export(h->work_d, d.first_block + g, w.t0, h->rec_w, d.wdtype, h->rec_tgt, h->rec_dly, h->hdr, d.n,
-                           t_begin, t_end, cnt, ds, dt, dd, dw, need, h->stream));
+    CUDA_TRY(launch_export(h->nets_d, h->work_d, d.first_block + g, h->n_warps, h->rec_w, d.wdtype, h->rec_meta,
+                           h->hdr, h->row_base, d.n, t_begin, t_end, cnt, ds, dt, dd, dw, need, h->stream));
   }
   unsigned long long got = 0;
   std::vector<int32_t> hs(need), ht(need), hd(need);
@@ -779,7 +801,7 @@ int cortex_deliver(cortex_net* h, int32_t net_idx, const int32_t* ids, int64_t n
   StepArgs a = make_args(h);
   a.n_steps = 1;
   a.phases = kPhaseDeliver;
-  a.ring_smem = 0;
+  a.ring_smem = h->ring_smem ? 1 : 0;
   a.raster_step = nullptr;
   a.raster_id = nullptr;
   a.t_fixed = t_emit;

@@ -86,7 +86,7 @@ __device__ __forceinline__ Draw2 draw_pair(const NetDev& d, uint32_t i, uint32_t
 // Targets of a wave: [t_lo, t_hi) of the network; block of target i = i / tb.
 __global__ void k_count(const NetDev* __restrict__ nets, int net_idx, int32_t t_lo, int32_t t_hi, int32_t tb,
                         int first_group, uint32_t* __restrict__ cnt) {
-  const NetDev d = nets[net_idx];
+  const NetDev& d = nets[net_idx];
   const int64_t pairs = (d.k + 1) / 2;
   const int64_t total = (int64_t)(t_hi - t_lo) * pairs;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -149,10 +149,69 @@ cudaError_t launch_scan_groups(uint32_t* cnt, uint32_t* cursor, int n_groups, in
   return cudaGetLastError();
 }
 
+// ---- rows of the CSR by source: per-block offsets inside each row, row starts -------------------
+// off[b][s] = sum over blocks b' < b of cnt[b'][s]; rowcnt[s] = sum over all blocks
+__global__ void k_colscan(const uint32_t* __restrict__ cnt_all, int nb, int32_t n, uint32_t* __restrict__ off_all,
+                          uint32_t* __restrict__ rowcnt) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t acc = 0;
+    for (int b = 0; b < nb; ++b) {
+      off_all[(int64_t)b * n + s] = acc;
+      acc += cnt_all[(int64_t)b * n + s];
+    }
+    rowcnt[s] = acc;
+  }
+}
+
+// row_base[s] = exclusive prefix of rowcnt over the sources (64-bit), one block
+__global__ void k_rowscan(const uint32_t* __restrict__ rowcnt, int32_t n, unsigned long long* __restrict__ row_base) {
+  __shared__ unsigned long long warp_sum[32];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int64_t off = 0; off < n; off += blockDim.x) {
+    const int64_t s = off + threadIdx.x;
+    const unsigned long long v = (s < n) ? rowcnt[s] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = (lane < nwarps) ? warp_sum[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nwarps) warp_sum[lane] = w;
+    }
+    __syncthreads();
+    if (s < n) row_base[s] = carry + (warp > 0 ? warp_sum[warp - 1] : 0ull) + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_sum[nwarps - 1];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_build_rows(const uint32_t* cnt_all, int nb, int32_t n, uint32_t* off_all, uint32_t* rowcnt,
+                              unsigned long long* row_base, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(4096, ((int64_t)n + 255) / 256);
+  k_colscan<<<std::max(blocks, 1), 256, 0, s>>>(cnt_all, nb, n, off_all, rowcnt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rowscan<<<1, 1024, 0, s>>>(rowcnt, n, row_base);
+  return cudaGetLastError();
+}
+
 // ---- fill: scatter keys into their (block, source) segments --------------------------------
 __global__ void k_fill(const NetDev* __restrict__ nets, int net_idx, int32_t t_lo, int32_t t_hi, int32_t tb,
                        int first_group, uint32_t* __restrict__ cursor, uint32_t* __restrict__ keys) {
-  const NetDev d = nets[net_idx];
+  const NetDev& d = nets[net_idx];
   const int64_t pairs = (d.k + 1) / 2;
   const int64_t total = (int64_t)(t_hi - t_lo) * pairs;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -182,32 +241,41 @@ cudaError_t launch_build_fill_net(const NetDev* nets_dev, int net_idx, int32_t n
 }
 
 // ---- finalize: sort each segment, write records and headers --------------------------------
+// Record of synapse (source s -> local target j, delay d): weight w and
+//   meta = ((j - wd * tw) << dbits) | (d - d_min),   wd = j / tw the delivery warp owning j.
 constexpr int kSegCap = 2048;  // keys sorted in shared memory per warp
 
 __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ nets, const BlockWork* __restrict__ work,
-                                                  int net_idx, int first_group, int n_groups, int n_warps_blk,
+                                                  int net_idx, int first_group, int n_groups, int n_dw,
                                                   const uint32_t* __restrict__ cnt,
                                                   const uint32_t* __restrict__ seg_end,
-                                                  const uint32_t* __restrict__ keys, void* __restrict__ rec_w,
-                                                  uint16_t* __restrict__ rec_tgt, uint8_t* __restrict__ rec_dly,
+                                                  const uint32_t* __restrict__ keys,
+                                                  const uint32_t* __restrict__ off_all,
+                                                  const unsigned long long* __restrict__ row_base,
+                                                  void* __restrict__ rec_w, uint16_t* __restrict__ rec_meta,
                                                   uint4* __restrict__ hdr, int32_t* __restrict__ err,
                                                   uint32_t* __restrict__ max_seg) {
   extern __shared__ uint32_t sk[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   uint32_t* buf = sk + wib * kSegCap;
-  const NetDev d = nets[net_idx];
-  const int64_t n_seg = (int64_t)n_groups * d.n;
+  const NetDev& d = nets[net_idx];
+  const int32_t n = d.n, n_exc = d.n_exc, k = d.k, d_min = d.d_min, dbits = d.dbits, wdtype = d.wdtype;
+  const int32_t nbk = d.n_blocks;
+  const int64_t rec_net = d.rec_base, hdr_net = d.hdr_base, row_off = d.row_off;
+  const float w_exc = d.w_exc, w_inh = d.w_inh;
+  const int64_t n_seg = (int64_t)n_groups * n;
   const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t warp_stride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t tb_full = work[d.first_block].nt;
   for (int64_t sg = warp_global; sg < n_seg; sg += warp_stride) {
-    const int64_t g = sg / d.n;
-    const uint32_t src = (uint32_t)(sg % d.n);
+    const int64_t g = sg / n;
+    const uint32_t src = (uint32_t)(sg % n);
     const BlockWork w = work[d.first_block + first_group + g];
     const uint32_t len = cnt[sg];
     const uint32_t end = seg_end[sg];
     const uint32_t start = end - len;
-    // keys of block g start at g * tb * K where tb = targets of a full block of this network
-    const int64_t key0 = g * (int64_t)work[d.first_block].nt * d.k + start;
+    // keys of block g start at g * tb * K (all blocks but the last hold tb targets)
+    const int64_t key0 = g * tb_full * k + start;
     if (len > kSegCap || len > 65535u) {
       if (lane == 0) atomicOr(err, kErrSegment);
       continue;
@@ -217,40 +285,42 @@ __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ net
     while (p2 < len) p2 <<= 1;
     for (uint32_t q = lane; q < p2; q += 32) buf[q] = (q < len) ? keys[key0 + q] : 0xffffffffu;
     __syncwarp();
-    // bitonic sort, ascending
-    for (uint32_t k = 2; k <= p2; k <<= 1) {
-      for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+    // bitonic sort, ascending: (local target, draw)
+    for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
+      for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
         for (uint32_t q = lane; q < p2; q += 32) {
           const uint32_t l = q ^ jj;
           if (l > q) {
-            const uint32_t a = buf[q], b = buf[l];
-            const bool up = (q & k) == 0;
-            if ((a > b) == up) {
-              buf[q] = b;
-              buf[l] = a;
+            const uint32_t x = buf[q], y = buf[l];
+            const bool up = (q & kk) == 0;
+            if ((x > y) == up) {
+              buf[q] = y;
+              buf[l] = x;
             }
           }
         }
         __syncwarp();
       }
     }
-    // records
-    const int64_t r0 = w.rec_base + start;
+    // the block's piece of the source's row (CSR by source, blocks in ascending order)
+    const uint32_t piece = off_all[(int64_t)(first_group + g) * n + src];
+    const int64_t r0 = rec_net + (int64_t)row_base[row_off + src] + piece;
     for (uint32_t q = lane; q < len; q += 32) {
       const uint32_t key = buf[q];
       const uint32_t local = key >> 16, j = key & 0xffffu;
       const Draw2 dr = draw_pair(d, (uint32_t)w.t0 + local, j >> 1);
       const uint32_t s2 = dr.src[j & 1u], dl = dr.dly[j & 1u];
       if (s2 != src) atomicOr(err, kErrBuild);
-      const float wv = (src < (uint32_t)d.n_exc) ? d.w_exc : d.w_inh;
-      if (d.wdtype == 1) reinterpret_cast<__nv_bfloat16*>(rec_w)[r0 + q] = __float2bfloat16_rn(wv);
+      const float wv = (src < (uint32_t)n_exc) ? w_exc : w_inh;
+      if (wdtype == 1) reinterpret_cast<__nv_bfloat16*>(rec_w)[r0 + q] = __float2bfloat16_rn(wv);
       else reinterpret_cast<float*>(rec_w)[r0 + q] = wv;
-      rec_tgt[r0 + q] = (uint16_t)local;
-      rec_dly[r0 + q] = (uint8_t)dl;
+      const uint32_t wd = local / (uint32_t)w.tw;
+      const uint32_t rel = local - wd * (uint32_t)w.tw;
+      rec_meta[r0 + q] = (uint16_t)((rel << dbits) | (dl - (uint32_t)d_min));
     }
-    // header: base, then for warp w the number of entries with local target < (w + 1) * tw
+    // header: base, then for delivery warp wd the number of entries with local target < (wd + 1) * tw
     uint32_t e_w = len;
-    if (lane < n_warps_blk) {
+    if (lane < n_dw) {
       const uint32_t bound = min((uint32_t)((lane + 1) * w.tw), (uint32_t)w.nt);
       uint32_t lo = 0, hi = len;  // first q with (buf[q] >> 16) >= bound
       while (lo < hi) {
@@ -260,18 +330,33 @@ __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ net
       }
       e_w = lo;
     }
+    // cells repeated inside a warp's piece (a source drawn twice by one target with one delay):
+    // flag the warp, whose delivery then adds that piece one entry at a time
+    __syncwarp();
+    uint32_t dup = 0;
+    for (uint32_t q = lane; q + 1 < len; q += 32) {
+      const uint32_t local = buf[q] >> 16;
+      for (uint32_t q2 = q + 1; q2 < len && (buf[q2] >> 16) == local; ++q2) {
+        const uint32_t j1 = buf[q] & 0xffffu, j2 = buf[q2] & 0xffffu;
+        const Draw2 d1 = draw_pair(d, (uint32_t)w.t0 + local, j1 >> 1);
+        const Draw2 d2 = draw_pair(d, (uint32_t)w.t0 + local, j2 >> 1);
+        if (d1.dly[j1 & 1u] == d2.dly[j2 & 1u]) dup |= 1u << (local / (uint32_t)w.tw);
+      }
+    }
+    dup = __reduce_or_sync(0xffffffffu, dup);
+    if (piece + len > 0xffffu && lane == 0) atomicOr(err, kErrSegment);  // rows longer than 65535
     uint32_t words[8];
-    words[0] = start;
+    words[0] = (piece & 0xffffu) | (dup << 16);
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-      const uint32_t a = __shfl_sync(0xffffffffu, e_w, 2 * q);
-      const uint32_t b = __shfl_sync(0xffffffffu, e_w, 2 * q + 1);
-      const uint32_t ea = (2 * q < n_warps_blk) ? a : len;
-      const uint32_t eb = (2 * q + 1 < n_warps_blk) ? b : len;
-      words[q + 1] = (ea & 0xffffu) | (eb << 16);
+      const uint32_t x = __shfl_sync(0xffffffffu, e_w, 2 * q);
+      const uint32_t y = __shfl_sync(0xffffffffu, e_w, 2 * q + 1);
+      const uint32_t ex = (2 * q < n_dw) ? x : len;
+      const uint32_t ey = (2 * q + 1 < n_dw) ? y : len;
+      words[q + 1] = (ex & 0xffffu) | (ey << 16);
     }
     if (lane == 0) {
-      const int64_t h = w.hdr_base + src;
+      const int64_t h = hdr_net + (int64_t)src * nbk + (first_group + g);
       hdr[2 * h] = make_uint4(words[0], words[1], words[2], words[3]);
       hdr[2 * h + 1] = make_uint4(words[4], words[5], words[6], words[7]);
     }
@@ -280,14 +365,15 @@ __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ net
 }
 
 cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* work_dev, int net_idx, int first_group,
-                                      int n_groups, int n_warps_blk, const uint32_t* cnt, const uint32_t* seg_end,
-                                      const uint32_t* keys, void* rec_w, uint16_t* rec_tgt, uint8_t* rec_dly,
+                                      int n_groups, int n_dw, const uint32_t* cnt, const uint32_t* seg_end,
+                                      const uint32_t* keys, const uint32_t* off_all,
+                                      const unsigned long long* row_base, void* rec_w, uint16_t* rec_meta,
                                       uint4* hdr, int32_t* err, uint32_t* max_seg, cudaStream_t s) {
   const size_t smem = 8 * kSegCap * sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_finalize<<<152 * 4, 256, smem, s>>>(nets_dev, work_dev, net_idx, first_group, n_groups, n_warps_blk, cnt,
-                                        seg_end, keys, rec_w, rec_tgt, rec_dly, hdr, err, max_seg);
+  k_finalize<<<152 * 4, 256, smem, s>>>(nets_dev, work_dev, net_idx, first_group, n_groups, n_dw, cnt, seg_end, keys,
+                                        off_all, row_base, rec_w, rec_meta, hdr, err, max_seg);
   return cudaGetLastError();
 }
 
@@ -296,7 +382,7 @@ cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* w
 // each operation rounded to float.  I = 0, refractory counter = 0.
 __global__ void k_init_state(const NetDev* __restrict__ nets, int net_idx, float* __restrict__ V,
                              float* __restrict__ I, int32_t* __restrict__ R) {
-  const NetDev d = nets[net_idx];
+  const NetDev& d = nets[net_idx];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, kStreamV0, 0u), d.seed_lo, d.seed_hi);
     const float frac = __fmul_rn((float)(r.x >> 8), 0x1p-24f);
@@ -334,41 +420,50 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 }
 
 // ---- export of the incoming synapses of a target range (connectivity checks) ------------------
-__global__ void k_export(const BlockWork* __restrict__ work, int block, const void* __restrict__ rec_w, int wdtype,
-                         const uint16_t* __restrict__ rec_tgt, const uint8_t* __restrict__ rec_dly,
-                         const uint4* __restrict__ hdr, int32_t n_src, int32_t t_begin, int32_t t_end,
+__global__ void k_export(const NetDev* __restrict__ nets, const BlockWork* __restrict__ work, int block, int n_dw,
+                         const void* __restrict__ rec_w, int wdtype, const uint16_t* __restrict__ rec_meta,
+                         const uint4* __restrict__ hdr, const unsigned long long* __restrict__ row_base,
+                         int32_t n_src, int32_t t_begin, int32_t t_end,
                          unsigned long long* counter, int32_t* o_src, int32_t* o_tgt, int32_t* o_dly, float* o_w,
                          int64_t cap) {
   const BlockWork w = work[block];
+  const NetDev& d = nets[w.net];
+  const uint32_t dmask = (1u << d.dbits) - 1u;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_src; s += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 h0 = hdr[2 * (w.hdr_base + s)];
-    const uint4 h1 = hdr[2 * (w.hdr_base + s) + 1];
+    const int64_t hi = d.hdr_base + s * d.n_blocks + w.group;
+    const uint4 h0 = hdr[2 * hi];
+    const uint4 h1 = hdr[2 * hi + 1];
     const uint32_t words[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-    const uint32_t base = words[0];
-    // total entries = the last warp's end; all unused ends equal the total
-    const uint32_t len = words[7] >> 16;
-    for (uint32_t q = 0; q < len; ++q) {
-      const int64_t r = w.rec_base + base + q;
-      const int32_t tgt = w.t0 + rec_tgt[r];
-      if (tgt < t_begin || tgt >= t_end) continue;
-      const unsigned long long pos = atomicAdd(counter, 1ull);
-      if ((int64_t)pos >= cap) continue;
-      o_src[pos] = (int32_t)s;
-      o_tgt[pos] = tgt;
-      o_dly[pos] = rec_dly[r];
-      o_w[pos] = wdtype == 1 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(rec_w)[r])
-                             : reinterpret_cast<const float*>(rec_w)[r];
+    const uint32_t base = words[0] & 0xffffu;
+    uint32_t e0 = 0;
+    for (int wd = 0; wd < n_dw; ++wd) {
+      const uint32_t word = words[1 + (wd >> 1)];
+      const uint32_t e1 = (wd & 1) ? (word >> 16) : (word & 0xffffu);
+      for (uint32_t q = e0; q < e1; ++q) {
+        const int64_t r = d.rec_base + (int64_t)row_base[d.row_off + s] + base + q;
+        const uint32_t meta = rec_meta[r];
+        const int32_t tgt = w.t0 + wd * w.tw + (int32_t)(meta >> d.dbits);
+        if (tgt < t_begin || tgt >= t_end) continue;
+        const unsigned long long pos = atomicAdd(counter, 1ull);
+        if ((int64_t)pos >= cap) continue;
+        o_src[pos] = (int32_t)s;
+        o_tgt[pos] = tgt;
+        o_dly[pos] = d.d_min + (int32_t)(meta & dmask);
+        o_w[pos] = wdtype == 1 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(rec_w)[r])
+                               : reinterpret_cast<const float*>(rec_w)[r];
+      }
+      e0 = e1;
     }
   }
 }
 
-cudaError_t launch_export(const BlockWork* work_dev, int block, int32_t, const void* rec_w, int wdtype,
-                          const uint16_t* rec_tgt, const uint8_t* rec_dly, const uint4* hdr, int32_t n_src,
-                          int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src, int32_t* tgt,
-                          int32_t* dly, float* w, int64_t cap, cudaStream_t s) {
+cudaError_t launch_export(const NetDev* nets_dev, const BlockWork* work_dev, int block, int n_dw, const void* rec_w,
+                          int wdtype, const uint16_t* rec_meta, const uint4* hdr, const unsigned long long* row_base,
+                          int32_t n_src, int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src,
+                          int32_t* tgt, int32_t* dly, float* w, int64_t cap, cudaStream_t s) {
   const int blocks = (int)std::min<int64_t>(1024, (n_src + 255) / 256);
-  k_export<<<max(blocks, 1), 256, 0, s>>>(work_dev, block, rec_w, wdtype, rec_tgt, rec_dly, hdr, n_src, t_begin, t_end,
-                                          counter, src, tgt, dly, w, cap);
+  k_export<<<std::max(blocks, 1), 256, 0, s>>>(nets_dev, work_dev, block, n_dw, rec_w, wdtype, rec_meta, hdr,
+                                               row_base, n_src, t_begin, t_end, counter, src, tgt, dly, w, cap);
   return cudaGetLastError();
 }
 

@@ -1,18 +1,23 @@
 // cortex_internal.cuh -- device-side data layout and helpers shared by the library's kernels.
 //
 // Layout in HBM (one handle, possibly many networks):
-//   records   SoA streams, one entry per synapse:  w (f32 or bf16), tgt (u16, target index local
-//             to its block), dly (u8, delay in steps).  Sorted by (block, source, target, draw):
-//             inside a block's sub-graph the synapses of one source are contiguous and ordered by
-//             target, so each warp's target sub-range is a contiguous piece of that segment.
-//   headers   one 32-byte header per (block, source):  u32 base (first record, relative to the
-//             block's record base) and u16 end[w] for the block's warps w = 0..n_w-1 (entries of
-//             warps 0..w); the segment of warp w is [base + end[w-1], base + end[w]).
+//   records   two streams, one entry per synapse: w (f32 or bf16) and meta (u16) =
+//             (target index relative to its delivery warp << dbits) | (delay - d_min).  Sorted by
+//             (source, block, target, draw): the CSR by source of the whole network, in which the
+//             synapses of one source are grouped by owning block and, inside a block, by target --
+//             so each delivery warp's target sub-range is a contiguous piece of its block's piece.
+//             All blocks read adjacent pieces of one spiking source's row (shared pages and rows).
+//   row_base  u64 per source: first record of the source's row, relative to the network's base.
+//   headers   one 32-byte header per (source, block), stored source-major: word 0 = first record of
+//             the block's piece relative to the row (low 16 bits) | flags (bit 16 + w: warp w's piece
+//             repeats a cell), then u16 end[w] for the block's delivery warps w = 0..13 (entries of
+//             warps 0..w; unused entries repeat the total).
 //   state     V (f32), I (f32), refractory counter (i32) per neuron.
 //   ring      per block [D][T_b] floats, D = d_max: cell (slot, j) holds the input due at the
 //             step t with t mod D == slot for local target j.
 //   pub       spike lists published per window: ids[(parity*W_max + ws) * n_total + pub_base + k],
-//             counts[(parity*W_max + ws) * n_blocks + block], flags[block] = windows completed.
+//             counts[(parity*W_max + ws) * n_blocks + block], mailbox[block] = (windows completed,
+//             count of the window's first step).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -21,8 +26,10 @@
 namespace cortex {
 
 constexpr int kPoissonCap = 64;     // Poisson threshold table entries
-constexpr int kMaxWarps = 14;       // warps per block (32-byte header: 4 + 2 * 14 bytes)
-constexpr int kSpikeBatch = 32;     // spikes staged per delivery round
+constexpr int kMaxWarps = 14;       // warps per block, all of them delivery warps (32-byte header: 4 + 2 * 14)
+constexpr int kSpikeBatch = 32;     // spikes staged per delivery round (at most)
+constexpr int kStages = 4;          // delivery rounds in flight per block
+constexpr int kIdCap = 2048;        // spike ids of a window kept in shared memory
 
 constexpr uint32_t kStreamConn = 1u;
 constexpr uint32_t kStreamV0 = 2u;
@@ -37,6 +44,7 @@ constexpr int kErrBuild = 8;
 struct NetDev {
   int32_t n, n_exc, n_inh, k_exc, k_inh, k;
   int32_t d_min, d_max, depth, window;        // depth D = d_max, window W = d_min
+  int32_t dbits;                               // bits of (delay - d_min) in a record's meta
   uint32_t seed_lo, seed_hi;
   int32_t wdtype;                              // 0 f32, 1 bf16
   int32_t first_block, n_blocks;               // blocks of this network in the work table
@@ -47,6 +55,9 @@ struct NetDev {
   // host-provided inputs for the propagator kernel
   float tau_m, c_m, tau_syn, t_ref, dt, nu_ext_hz, j_exc_in, j_inh_in;
   int64_t neuron_base;                         // offset of this network in V / I / R
+  int64_t rec_base;                            // first record of this network
+  int64_t hdr_base;                            // first header of this network (source-major)
+  int64_t row_off;                             // offset of this network in row_base
   int64_t raster_base, raster_cap;             // offset and capacity in the raster arrays
   uint32_t thr[kPoissonCap];
 };
@@ -71,16 +82,16 @@ struct StepArgs {
   int32_t w_max;                  // largest window over the networks
   int64_t n_total;                // neurons over all networks (publication stride)
   const void* rec_w;
-  const uint16_t* rec_tgt;
-  const uint8_t* rec_dly;
+  const uint16_t* rec_meta;
   const uint4* hdr;               // 2 x uint4 per header
+  const unsigned long long* row_base;
   float* V;
   float* I;
   int32_t* R;
   float* ring;
   uint32_t* pub_ids;
   uint32_t* pub_cnt;
-  uint32_t* pub_flag;
+  unsigned long long* pub_flag;   // mailbox per block: windows completed | count of ws 0 << 32
   int32_t* raster_step;
   int32_t* raster_id;
   unsigned long long* raster_count;   // per network: spikes emitted so far
@@ -91,6 +102,8 @@ struct StepArgs {
   int32_t phases;                     // kPhaseUpdate | kPhaseDeliver
   int32_t ring_smem;                  // 1: ring slice in shared memory
   int32_t stage_bytes;                // shared staging capacity for record segments
+  int32_t batch;                      // spikes per delivery round
+  int32_t cap_w, cap_m;               // staging bytes per spike: weight stream, meta stream
   int32_t max_nt, max_depth, max_nb;  // shared-memory layout maxima over the blocks
   long long timeout_ns;
   // delivery-only launches (cortex_deliver): fixed emission step
@@ -145,6 +158,17 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+
 // ---- mbarrier and bulk copy (TMA, non-tensor) ----------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -162,6 +186,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
@@ -177,6 +205,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_addr(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), tracked per thread
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// arrive on the mbarrier once all of this thread's earlier cp.async copies have landed; the
+// arrival counts against the count the barrier was initialised with
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
@@ -197,11 +243,14 @@ cudaError_t launch_build_count_net(const NetDev* nets_dev, int net_idx, int32_t 
                                    int32_t tb, uint32_t* cnt, cudaStream_t s);
 cudaError_t launch_scan_groups(uint32_t* cnt, uint32_t* cursor, int n_groups, int32_t n_src, uint32_t* tmp,
                                cudaStream_t s);
+cudaError_t launch_build_rows(const uint32_t* cnt_all, int nb, int32_t n, uint32_t* off_all, uint32_t* rowcnt,
+                              unsigned long long* row_base, cudaStream_t s);
 cudaError_t launch_build_fill_net(const NetDev* nets_dev, int net_idx, int32_t n, int first_group, int n_groups,
                                   int32_t tb, uint32_t* cursor, uint32_t* keys, cudaStream_t s);
 cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* work_dev, int net_idx, int first_group,
                                       int n_groups, int n_warps_blk, const uint32_t* cnt, const uint32_t* seg_end,
-                                      const uint32_t* keys, void* rec_w, uint16_t* rec_tgt, uint8_t* rec_dly,
+                                      const uint32_t* keys, const uint32_t* off_all,
+                                      const unsigned long long* row_base, void* rec_w, uint16_t* rec_meta,
                                       uint4* hdr, int32_t* err, uint32_t* max_seg, cudaStream_t s);
 cudaError_t launch_init_state(const NetDev* net_host, const NetDev* net_dev, int net_idx, float* V, float* I,
                               int32_t* R, cudaStream_t s);
@@ -209,10 +258,11 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s);
 cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s);
 size_t step_smem_bytes(int max_nt, int max_depth, int w_max, int max_nb, bool ring_smem, int stage_bytes);
+void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m);
 cudaError_t step_kernel_attributes(size_t smem);
-int step_occupancy(int threads, size_t smem);
-cudaError_t launch_export(const BlockWork* work_dev, int block, int32_t t0_net, const void* rec_w, int wdtype,
-                          const uint16_t* rec_tgt, const uint8_t* rec_dly, const uint4* hdr, int32_t n_src,
-                          int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src, int32_t* tgt,
-                          int32_t* dly, float* w, int64_t cap, cudaStream_t s);
+int step_occupancy(int threads, size_t smem, bool ring_smem);
+cudaError_t launch_export(const NetDev* nets_dev, const BlockWork* work_dev, int block, int n_dw, const void* rec_w,
+                          int wdtype, const uint16_t* rec_meta, const uint4* hdr, const unsigned long long* row_base,
+                          int32_t n_src, int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src,
+                          int32_t* tgt, int32_t* dly, float* w, int64_t cap, cudaStream_t s);
 }  // namespace cortex

@@ -78,6 +78,15 @@ CONFIGS = {
                name="batch64_brunel_n2k-50k"),
 }
 
+# Profiling cases: the c1 and c3 models at a quarter of the neurons and of the in-degree (same
+# K/N, so the same per-block segment structure per source), small enough for ncu replay.
+PROFILE = {
+    "c1q": dict(spec=NetSpec(22500, 5625, 2250, 562), steps=2000, seed=BASE_SEED + 11,
+                name="brunel_n28125_k2812_fp32"),
+    "c3q": dict(spec=NetSpec(200000, 50000, 2250, 562, weight_dtype=BF16), steps=2000, seed=BASE_SEED + 13,
+                name="brunel_n250k_k2812_bf16"),
+}
+
 # Same statistics as c3 at 10,000 neurons (K = 11,250 > N, so sources repeat).
 C3_SUBSAMPLE = dict(spec=NetSpec(8000, 2000, 9000, 2250, weight_dtype=BF16), steps=10000,
                     seed=BASE_SEED + 3, name="brunel_n10k_k11250_bf16")
