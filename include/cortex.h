@@ -168,6 +168,26 @@ int cortex_deliver(cortex_net* net, int32_t net_idx, const int32_t* ids, int64_t
  * host arrays).  Used to check the device generator against its published definition. */
 int cortex_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 
+/* The incoming synapses of targets [t_begin, t_end) of the network described by params and seed
+ * -- the same Philox connectivity cortex_build draws -- as a CSR by source, computed WITHOUT
+ * allocating any device memory.  The paper has no counterpart: this exists for callers that cannot
+ * call the device allocator when they need connectivity (for example while another framework owns
+ * the whole device memory pool).  All output pointers are DEVICE pointers owned by the caller:
+ * row_ptr[n + 1] (n = n_exc + n_inh; synapses of source s are entries row_ptr[s]..row_ptr[s+1]-1,
+ * ordered by target), tgt/delay/weight[(t_end - t_begin) * (k_exc + k_inh)] (delay in steps,
+ * weight as stored: bfloat16-rounded when weight_dtype is CORTEX_BF16).  Work is issued on stream
+ * and the call synchronises it.
+ * Working memory is one static 8 MiB device array per GPU: (n + 1) + (t_end - t_begin) * K must be
+ * at most 2^21 words, t_end - t_begin at most 65536, and no source may have more than 2048
+ * synapses in the range; larger sizes return CORTEX_ERR_UNSUPPORTED without launching anything.
+ * The first call on a device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  Every call reuses the same array (it is cleared
+ * at the start of each call), so calls that overlap on the GPU -- on different streams or host
+ * threads -- race and must be serialised by the caller.  Errors: CORTEX_ERR_ARG (bad parameters
+ * or NULL outputs), CORTEX_ERR_UNSUPPORTED (size limits), CORTEX_ERR_CUDA. */
+int cortex_subgraph_noalloc(const cortex_params* params, uint64_t seed, int32_t t_begin, int32_t t_end,
+                            void* stream, int32_t* row_ptr, int32_t* tgt, int32_t* delay, float* weight);
+
 /* Release everything the handle owns.  NULL is allowed. */
 void cortex_free(cortex_net* net);
 

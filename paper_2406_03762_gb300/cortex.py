@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
 EXPORTED = [
     "cortex_build", "cortex_build_batch", "cortex_simulate", "cortex_spikes", "cortex_clear_spikes",
     "cortex_stats", "cortex_export_synapses", "cortex_get_state", "cortex_constants", "cortex_deliver",
-    "cortex_philox", "cortex_free", "cortex_strerror", "cortex_last_error",
+    "cortex_philox", "cortex_free", "cortex_strerror", "cortex_last_error", "cortex_subgraph_noalloc",
 ]
 
 _lib = None
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = False):
     L.cortex_deliver.argtypes = [vp, ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int64, ctypes.c_int64,
                                  ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_int64)]
     L.cortex_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int64, P(ctypes.c_uint32)]
+    L.cortex_subgraph_noalloc.argtypes = [P(Params), ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("cortex_free", "cortex_strerror", "cortex_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -256,3 +257,12 @@ def philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
     _check(load().cortex_philox(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), len(c), _p(out, ctypes.c_uint32)),
            "cortex_philox")
     return out
+
+
+def subgraph_noalloc(spec, seed: int, t_begin: int, t_end: int, row_ptr, tgt, delay, weight, stream=None):
+    """cortex_subgraph_noalloc: the caller passes device buffers (anything with data_ptr(), e.g.
+    torch CUDA tensors: int32 row_ptr[n + 1], int32 tgt/delay[nnz], float32 weight[nnz])."""
+    p = params_from_spec(spec)
+    ptr = lambda t: ctypes.c_void_p(int(t.data_ptr())) if t is not None else None
+    _check(load().cortex_subgraph_noalloc(ctypes.byref(p), int(seed), int(t_begin), int(t_end), _stream_handle(stream),
+                                          ptr(row_ptr), ptr(tgt), ptr(delay), ptr(weight)), "cortex_subgraph_noalloc")
