@@ -512,36 +512,41 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
           const uint32_t total = __shfl_sync(0xffffffffu, c_end, 31);
           if (lane == 0) my_events += total;
           int cur = -1;
-          for (uint32_t e = 0; e < total; e += 4 * 32) {
+          // key and weight of the lane's entry in the chunk starting at cb (0xffffffff: none)
+          auto chunk_key = [&](uint32_t cb, float& wv) -> uint32_t {
+            const uint32_t bits = (lane < n_ne && c_start >= cb && c_start < cb + 32) ? (1u << (c_start - cb)) : 0u;
+            const uint32_t sm = __reduce_or_sync(0xffffffffu, bits);
+            const int seg = cur + __popc(sm & (0xffffffffu >> (31 - lane)));
+            cur += __popc(sm);
+            const uint32_t q = cb + lane;
+            const int sl = seg & 31;
+            const uint32_t swb = __shfl_sync(0xffffffffu, c_wb, sl);
+            const uint32_t smb = __shfl_sync(0xffffffffu, c_mb, sl);
+            const uint32_t scs = __shfl_sync(0xffffffffu, c_start, sl);
+            const uint32_t stm = __shfl_sync(0xffffffffu, c_tm, sl);
+            wv = 0.0f;
+            if (q >= total) return 0xffffffffu;
+            const uint32_t m = q - scs;
+            const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + smb + 2u * m);
+            wv = bf16 ? __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + swb + 2u * m))
+                      : *reinterpret_cast<const float*>(stage + swb + 4u * m);
+            int slot = (int)stm + d_min + (int)(meta & dmask);
+            if (slot >= D) slot -= D;
+            return (uint32_t)slot * (uint32_t)nt + wbase_t + (meta >> dbits);
+          };
+          uint32_t e = 0;
+          for (; e + 3 * 32 < total; e += 4 * 32) {  // four chunks at a time while they are all used
             uint32_t key[4];
             float wv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t cb = e + 32u * u;
-              const uint32_t bits = (lane < n_ne && c_start >= cb && c_start < cb + 32) ? (1u << (c_start - cb)) : 0u;
-              const uint32_t sm = __reduce_or_sync(0xffffffffu, bits);
-              const int seg = cur + __popc(sm & (0xffffffffu >> (31 - lane)));
-              cur += __popc(sm);
-              const uint32_t q = cb + lane;
-              const int sl = seg & 31;
-              const uint32_t swb = __shfl_sync(0xffffffffu, c_wb, sl);
-              const uint32_t smb = __shfl_sync(0xffffffffu, c_mb, sl);
-              const uint32_t scs = __shfl_sync(0xffffffffu, c_start, sl);
-              const uint32_t stm = __shfl_sync(0xffffffffu, c_tm, sl);
-              key[u] = 0xffffffffu;
-              wv[u] = 0.0f;
-              if (q < total) {
-                const uint32_t m = q - scs;
-                const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + smb + 2u * m);
-                wv[u] = bf16 ? __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + swb + 2u * m))
-                             : *reinterpret_cast<const float*>(stage + swb + 4u * m);
-                int slot = (int)stm + d_min + (int)(meta & dmask);
-                if (slot >= D) slot -= D;
-                key[u] = (uint32_t)slot * (uint32_t)nt + wbase_t + (meta >> dbits);
-              }
-            }
+            for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) fold_chunk<kRingSmem>(ring, wtags, key[u], wv[u], lane);
+          }
+          for (; e < total; e += 32) {
+            float wv;
+            const uint32_t key = chunk_key(e, wv);
+            fold_chunk<kRingSmem>(ring, wtags, key, wv, lane);
           }
         }
         if (have_next) {
