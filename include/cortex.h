@@ -37,7 +37,7 @@ extern "C" {
 #define CORTEX_ERR_ARG (-1)          /* invalid argument or size; nothing was changed */
 #define CORTEX_ERR_OOM (-2)          /* device or host allocation failed */
 #define CORTEX_ERR_CUDA (-3)         /* a CUDA runtime call failed (see cortex_last_error) */
-#define CORTEX_ERR_TIMEOUT (-4)      /* a device-side wait gave up; the handle stays usable */
+#define CORTEX_ERR_TIMEOUT (-4)      /* a device-side wait gave up; the CUDA context stays usable */
 #define CORTEX_ERR_UNSUPPORTED (-5)  /* sizes outside the supported range, or no capable GPU */
 #define CORTEX_ERR_OVERFLOW (-6)     /* an output buffer was too small (needed size returned) */
 
@@ -78,6 +78,10 @@ typedef struct cortex_options {
   int32_t use_graph;                 /* 0 = auto (on), 1 = on, -1 = off */
   int64_t raster_capacity;           /* 0 = auto; spikes kept on the device per network */
   double barrier_timeout_ms;         /* 0 = 2000 ms; device waits give up after this */
+  int32_t test_withhold_block;       /* test hook, 0 = off.  b + 1: block b of the persistent
+                                        kernel never publishes its spikes, so every block's bounded
+                                        wait at the window barrier runs out and cortex_simulate
+                                        returns CORTEX_ERR_TIMEOUT (error path of the barrier) */
 } cortex_options;
 
 typedef struct cortex_stats_t {
@@ -120,7 +124,8 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
 /* Advance every network by n_steps >= 0 steps from the current step (Sec. II-B loop: deliver,
  * update, compact spikes).  Continuing in pieces gives the same result as one call.
  * Synchronises the stream.  Errors: CORTEX_ERR_ARG, CORTEX_ERR_TIMEOUT (a grid-barrier or copy
- * wait gave up; state is undefined but the handle can be freed), CORTEX_ERR_CUDA.  If the
+ * wait gave up; the simulation state is undefined, later cortex_simulate calls on the handle
+ * return CORTEX_ERR_TIMEOUT at once, and the handle can still be freed), CORTEX_ERR_CUDA.  If the
  * device raster is full, spikes keep being simulated and counted but no longer recorded, and
  * the call returns CORTEX_ERR_OVERFLOW after finishing all steps. */
 int cortex_simulate(cortex_net* net, int64_t n_steps);
@@ -149,8 +154,8 @@ int cortex_export_synapses(cortex_net* net, int32_t net_idx, int32_t t_begin, in
  * synaptic current (pA), remaining refractory steps.  Any pointer may be NULL. */
 int cortex_get_state(cortex_net* net, int32_t net_idx, float* v, float* i_syn, int32_t* refr);
 
-/* The FP32 constants network net_idx uses, as computed on the device: out6 = {P11, P21, P22,
- * w_exc, w_inh, j_ext}; thr = Poisson thresholds (up to 64 words), *n_thr their count,
+/* The FP32 constants network net_idx uses, as computed on the device: out6 = {P11, P21,
+ * P22 - 1 (= expm1(-h/tau_m), the form the update uses), w_exc, w_inh, j_ext}; thr = Poisson thresholds (up to 64 words), *n_thr their count,
  * *n_ref the refractory steps. */
 int cortex_constants(cortex_net* net, int32_t net_idx, float* out6, uint32_t* thr,
                      int32_t* n_thr, int32_t* n_ref);

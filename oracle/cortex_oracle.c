@@ -112,12 +112,16 @@ float oracle_round_bf16(float x) {
  *            P22 = exp(-h/tau_m)
  *            P21 = tau_m tau_syn / (C (tau_syn - tau_m)) (P11 - P22)
  *            P20 = tau_m / C (1 - P22)
- * V is measured relative to E_L.  n_ref = round(t_ref / h) steps of clamping (Eq. 2). */
-typedef struct { double p11, p21, p22, p20; int32_t n_ref; } props64;
+ * V is measured relative to E_L.  n_ref = round(t_ref / h) steps of clamping (Eq. 2).
+ * The update is evaluated as V + ((P22 - 1) V + P21 I) with P22 - 1 = expm1(-h/tau_m): the same
+ * map, but P22 lies within 1% of 1, and its float rounding, divided by 1 - P22 in the stationary
+ * potential, would bias V by up to ~3e-6 relative; P22 - 1 rounds with 6e-8 relative error. */
+typedef struct { double p11, p21, p22, p20, p22m1; int32_t n_ref; } props64;
 
 static props64 compute_props(double tau_m, double c_m, double tau_syn, double t_ref, double h) {
   props64 q;
   q.p22 = exp(-h / tau_m);
+  q.p22m1 = expm1(-h / tau_m);
   q.p11 = exp(-h / tau_syn);
   q.p21 = tau_m * tau_syn / (c_m * (tau_syn - tau_m)) * (q.p11 - q.p22);
   q.p20 = tau_m / c_m * (1.0 - q.p22);
@@ -128,12 +132,13 @@ static props64 compute_props(double tau_m, double c_m, double tau_syn, double t_
 /* FP32 mode takes its parameters as the float values a float parameter record would hold. */
 static double as_f(double x) { return (double)(float)x; }
 
-void oracle_propagators(const oracle_params* p, double out64[4], float out32[4], int32_t* n_ref) {
+void oracle_propagators(const oracle_params* p, double out64[5], float out32[5], int32_t* n_ref) {
   props64 q = compute_props(p->tau_m, p->c_m, p->tau_syn, p->t_ref, p->dt);
-  out64[0] = q.p11; out64[1] = q.p21; out64[2] = q.p22; out64[3] = q.p20;
+  out64[0] = q.p11; out64[1] = q.p21; out64[2] = q.p22; out64[3] = q.p20; out64[4] = q.p22m1;
   props64 f = compute_props(as_f(p->tau_m), as_f(p->c_m), as_f(p->tau_syn), as_f(p->t_ref),
                             as_f(p->dt));
   out32[0] = (float)f.p11; out32[1] = (float)f.p21; out32[2] = (float)f.p22; out32[3] = (float)f.p20;
+  out32[4] = (float)f.p22m1;
   *n_ref = (p->precision == ORACLE_FP32) ? f.n_ref : q.n_ref;
 }
 
@@ -221,8 +226,8 @@ typedef struct oracle_net {
   double* v64; double* i64; double* ring64;    /* FP64 mode */
   int32_t* refr;
   /* constants */
-  float p11f, p21f, p22f, p20f, vthf, vresetf, wexf, winf, jextf, ief;
-  double p11, p21, p22, p20;
+  float p11f, p21f, p22f, p20f, p22m1f, vthf, vresetf, wexf, winf, jextf, ief;
+  double p11, p21, p22, p20, p22m1;
   int32_t n_ref;
   uint32_t thr[POISSON_TABLE_CAP];
   int n_thr;
@@ -256,10 +261,10 @@ static int init_common(oracle_net* net, const oracle_params* p, uint64_t seed) {
   net->seed = seed;
   net->n = (int64_t)p->n_exc + p->n_inh;
   net->depth = p->d_max + 1;
-  double o64[4]; float o32[4]; int32_t nref;
+  double o64[5]; float o32[5]; int32_t nref;
   oracle_propagators(p, o64, o32, &nref);
-  net->p11 = o64[0]; net->p21 = o64[1]; net->p22 = o64[2]; net->p20 = o64[3];
-  net->p11f = o32[0]; net->p21f = o32[1]; net->p22f = o32[2]; net->p20f = o32[3];
+  net->p11 = o64[0]; net->p21 = o64[1]; net->p22 = o64[2]; net->p20 = o64[3]; net->p22m1 = o64[4];
+  net->p11f = o32[0]; net->p21f = o32[1]; net->p22f = o32[2]; net->p20f = o32[3]; net->p22m1f = o32[4];
   net->n_ref = nref;
   net->vthf = (float)p->v_th; net->vresetf = (float)p->v_reset;
   net->wexf = (float)p->j_exc; net->winf = (float)p->j_inh;
@@ -425,7 +430,7 @@ static int push_spike(oracle_net* net, int64_t t, int32_t id) {
  *   1. in  = ring[i][t mod D]; the cell is cleared.
  *   2. k   = Poisson draw; ext = k * J_ext.
  *   3. refractory: V = V_reset and the counter counts down; otherwise
- *      V = fma(P22, V, P21 * I) with the old I (+ P20 * I_e when a bias current is set).
+ *      V = V + fma(P22 - 1, V, P21 * I) with the old I (+ P20 * I_e when a bias current is set).
  *   4. I = fma(P11, I, in); I = I + ext.
  *   5. V >= V_th: spike, V = V_reset, counter = n_ref (Eq. 2). */
 static int step_neuron_f32(oracle_net* net, int64_t i, int64_t t) {
@@ -438,7 +443,8 @@ static int step_neuron_f32(oracle_net* net, int64_t i, int64_t t) {
     net->refr[i] -= 1;
   } else {
     float pi = net->p21f * cur;
-    v = fmaf(net->p22f, v, pi);
+    float dv = fmaf(net->p22m1f, v, pi);
+    v = v + dv;
     if (net->ief != 0.0f) v = v + net->p20f * net->ief;
   }
   cur = fmaf(net->p11f, cur, in);
@@ -468,7 +474,7 @@ static int step_neuron_f64(oracle_net* net, int64_t i, int64_t t) {
     net->refr[i] -= 1;
   } else {
     double pi = net->p21 * cur;
-    v = fma(net->p22, v, pi);
+    v = v + fma(net->p22m1, v, pi);
     if (net->p.i_e != 0.0) v = v + net->p20 * net->p.i_e;
   }
   cur = fma(net->p11, cur, in);
@@ -601,7 +607,7 @@ void oracle_accounting(const oracle_net* net, int64_t* events, double* weight) {
 
 /* Float constants the FP32 mode uses (for comparison with a float parameter record). */
 void oracle_constants_f32(const oracle_net* net, float* out8, uint32_t* thr, int32_t* n_thr, int32_t* n_ref) {
-  out8[0] = net->p11f; out8[1] = net->p21f; out8[2] = net->p22f; out8[3] = net->p20f;
+  out8[0] = net->p11f; out8[1] = net->p21f; out8[2] = net->p22m1f; out8[3] = net->p20f;
   out8[4] = net->wexf; out8[5] = net->winf; out8[6] = net->jextf; out8[7] = net->vthf;
   for (int k = 0; k < net->n_thr; ++k) thr[k] = net->thr[k];
   *n_thr = net->n_thr;
@@ -618,4 +624,85 @@ void oracle_set_state(oracle_net* net, const double* v, const double* cur, const
     else { net->v64[i] = v[i]; net->i64[i] = cur[i]; }
     net->refr[i] = refr[i];
   }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Replay of a few targets                                                                     */
+/* ------------------------------------------------------------------------------------------ */
+/* The trajectory of a neuron depends only on its own incoming synapses and on the spikes their
+ * sources emitted (Eq. 1-3: the input at step t is the sum of the weights whose spikes arrive at
+ * t).  So a given raster of the whole network -- every (step, id) emitted, sorted by step then id
+ * -- determines each target's input exactly, and one target can be simulated alone.
+ *
+ * oracle_replay() does that for the ascending, distinct targets[0..n_t): each target draws its
+ * K_E + K_I incoming synapses as oracle_build() does; the synapses onto the chosen targets are
+ * kept as outgoing lists sorted by (source, target, draw index); for t = 0 .. n_steps-1 every
+ * chosen target is updated (step_neuron_f32 / _f64, consuming ring slot t), then every raster
+ * spike of step t is delivered onto the chosen targets (deliver(), same order as the full
+ * simulation).  The targets' own spikes are written to out_step/out_id (up to cap; *out_n is the
+ * count, which may exceed cap) and their final V, I, refractory counts to v/cur/refr (widened to
+ * double).  The raster is taken as given: a target's own replayed spikes are not fed back, so a
+ * run of the full oracle replays to itself exactly, and a raster from another simulator is
+ * checked one target at a time. */
+int oracle_replay(const oracle_params* p, uint64_t seed, int64_t n_t, const int32_t* targets,
+                  int64_t n_steps, int64_t n_spk, const int64_t* spk_step, const int32_t* spk_id,
+                  int64_t cap, int64_t* out_step, int32_t* out_id, int64_t* out_n,
+                  double* v, double* cur, int32_t* refr) {
+  if (!validate(p) || n_t < 0 || n_steps < 0 || n_spk < 0 || cap < 0 || !out_n) return ORACLE_ERR_ARG;
+  const int64_t n = (int64_t)p->n_exc + p->n_inh;
+  for (int64_t q = 0; q < n_t; ++q)
+    if (targets[q] < 0 || targets[q] >= n || (q > 0 && targets[q] <= targets[q - 1])) return ORACLE_ERR_ARG;
+  for (int64_t e = 0; e < n_spk; ++e) {
+    if (spk_id[e] < 0 || spk_id[e] >= n || spk_step[e] < 0) return ORACLE_ERR_ARG;
+    if (e > 0 && (spk_step[e] < spk_step[e - 1] || (spk_step[e] == spk_step[e - 1] && spk_id[e] <= spk_id[e - 1])))
+      return ORACLE_ERR_ARG;
+  }
+  oracle_net* net = (oracle_net*)calloc(1, sizeof(oracle_net));
+  if (!net) return ORACLE_ERR_OOM;
+  int rc = init_common(net, p, seed);
+  if (rc != ORACLE_OK) { oracle_free(net); return rc; }
+  const int64_t k = (int64_t)p->k_exc + p->k_inh;
+  net->n_syn = n_t * k;
+  net->row = (int64_t*)xcalloc((size_t)n + 1, sizeof(int64_t));
+  net->out_tgt = (int32_t*)xcalloc((size_t)net->n_syn, sizeof(int32_t));
+  net->out_dly = (uint8_t*)xcalloc((size_t)net->n_syn, sizeof(uint8_t));
+  int64_t* cursor = (int64_t*)xcalloc((size_t)n + 1, sizeof(int64_t));
+  if (!net->row || !net->out_tgt || !net->out_dly || !cursor) { free(cursor); oracle_free(net); return ORACLE_ERR_OOM; }
+  int32_t s, d;
+  for (int64_t q = 0; q < n_t; ++q)
+    for (int64_t j = 0; j < k; ++j) {
+      oracle_draw(seed, p->n_exc, p->n_inh, p->k_exc, p->d_min, p->d_max, targets[q], j, &s, &d);
+      net->row[s + 1] += 1;
+    }
+  for (int64_t x = 0; x < n; ++x) net->row[x + 1] += net->row[x];
+  for (int64_t x = 0; x < n; ++x) cursor[x] = net->row[x];
+  for (int64_t q = 0; q < n_t; ++q)  /* ascending targets, ascending draws: (source, target, draw) order */
+    for (int64_t j = 0; j < k; ++j) {
+      oracle_draw(seed, p->n_exc, p->n_inh, p->k_exc, p->d_min, p->d_max, targets[q], j, &s, &d);
+      int64_t pos = cursor[s]++;
+      net->out_tgt[pos] = targets[q];
+      net->out_dly[pos] = (uint8_t)d;
+    }
+  free(cursor);
+  int64_t e = 0, got = 0;
+  for (int64_t t = 0; t < n_steps; ++t) {
+    for (int64_t q = 0; q < n_t; ++q) {
+      int sp = (p->precision == ORACLE_FP32) ? step_neuron_f32(net, targets[q], t) : step_neuron_f64(net, targets[q], t);
+      if (sp) {
+        if (got < cap) { out_step[got] = t; out_id[got] = targets[q]; }
+        ++got;
+      }
+    }
+    while (e < n_spk && spk_step[e] < t) ++e;
+    while (e < n_spk && spk_step[e] == t) { deliver(net, spk_id[e], t); ++e; }
+  }
+  *out_n = got;
+  for (int64_t q = 0; q < n_t; ++q) {
+    int32_t i = targets[q];
+    if (v) v[q] = (p->precision == ORACLE_FP32) ? (double)net->v32[i] : net->v64[i];
+    if (cur) cur[q] = (p->precision == ORACLE_FP32) ? (double)net->i32[i] : net->i64[i];
+    if (refr) refr[q] = net->refr[i];
+  }
+  oracle_free(net);
+  return ORACLE_OK;
 }

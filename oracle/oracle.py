@@ -122,6 +122,11 @@ def lib():
         L.oracle_v0_word.restype = ctypes.c_uint32
         L.oracle_poisson_word.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
         L.oracle_poisson_word.restype = ctypes.c_uint32
+        L.oracle_replay.argtypes = [P(_Params), ctypes.c_uint64, ctypes.c_int64, P(ctypes.c_int32), ctypes.c_int64,
+                                    ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int32), ctypes.c_int64,
+                                    P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_double),
+                                    P(ctypes.c_double), P(ctypes.c_int32)]
+        L.oracle_replay.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -174,9 +179,9 @@ def round_bf16(x: float) -> float:
 
 
 def propagators(p: Params):
-    """Returns (p64[P11, P21, P22, P20] float64, p32[...] float32, n_ref)."""
-    o64 = np.zeros(4, dtype=np.float64)
-    o32 = np.zeros(4, dtype=np.float32)
+    """Returns (p64[P11, P21, P22, P20, P22 - 1] float64, p32[...] float32, n_ref)."""
+    o64 = np.zeros(5, dtype=np.float64)
+    o32 = np.zeros(5, dtype=np.float32)
     nref = ctypes.c_int32(0)
     cp = p.c()
     lib().oracle_propagators(ctypes.byref(cp), _ptr(o64, ctypes.c_double), _ptr(o32, ctypes.c_float),
@@ -220,6 +225,35 @@ def v0_word(seed: int, i: int) -> int:
 
 def poisson_word(seed: int, i: int, t: int) -> int:
     return int(lib().oracle_poisson_word(seed, i, t))
+
+
+def replay(p: Params, seed: int, targets, n_steps: int, raster_steps, raster_ids):
+    """Simulate only the given targets of the Philox network, driven by a given raster of the whole
+    network (its (step, id) pairs sorted by step, then id).  Returns (spike steps, spike ids) of the
+    targets, in (step, id) order, and their final (V, I, refractory count) as arrays in target
+    order.  A target's trajectory depends only on its own incoming synapses and the raster, so
+    this checks a large simulation one neuron at a time."""
+    t = np.ascontiguousarray(np.unique(np.asarray(targets, dtype=np.int32)))
+    rs = np.ascontiguousarray(np.asarray(raster_steps, dtype=np.int64))
+    ri = np.ascontiguousarray(np.asarray(raster_ids, dtype=np.int32))
+    cap = max(1024, 4 * len(t) * max(1, n_steps // 20))
+    while True:
+        os_ = np.empty(cap, dtype=np.int64)
+        oi = np.empty(cap, dtype=np.int32)
+        n_out = ctypes.c_int64(0)
+        v = np.empty(len(t), dtype=np.float64)
+        c = np.empty(len(t), dtype=np.float64)
+        r = np.empty(len(t), dtype=np.int32)
+        pc = p.c()
+        rc = lib().oracle_replay(ctypes.byref(pc), seed, len(t), _ptr(t, ctypes.c_int32), n_steps, len(rs),
+                                 _ptr(rs, ctypes.c_int64), _ptr(ri, ctypes.c_int32), cap,
+                                 _ptr(os_, ctypes.c_int64), _ptr(oi, ctypes.c_int32), ctypes.byref(n_out),
+                                 _ptr(v, ctypes.c_double), _ptr(c, ctypes.c_double), _ptr(r, ctypes.c_int32))
+        if rc != 0:
+            raise RuntimeError(f"oracle_replay failed ({rc})")
+        if n_out.value <= cap:
+            return os_[:n_out.value], oi[:n_out.value], (v, c, r)
+        cap = int(n_out.value)
 
 
 class Network:

@@ -42,6 +42,7 @@ class Options(ctypes.Structure):
         ("ring", ctypes.c_int32), ("mode", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
         ("targets_per_block", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("raster_capacity", ctypes.c_int64), ("barrier_timeout_ms", ctypes.c_double),
+        ("test_withhold_block", ctypes.c_int32),
     ]
 
 

@@ -81,6 +81,8 @@ struct cortex_net {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   long long timeout_ns = 2000000000ll;
+  int32_t withhold_block = -1;
+  bool timed_out = false;  // a device wait gave up: the barrier epochs are inconsistent
   uint32_t max_seg_len = 0;
   // bookkeeping
   int64_t step = 0;
@@ -162,7 +164,10 @@ int check_err(cortex_net* h, const char* where) {
   int32_t e = 0;
   CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  if (e & kErrTimeout) return fail(CORTEX_ERR_TIMEOUT, std::string(where) + ": a device wait timed out");
+  if (e & kErrTimeout) {
+    h->timed_out = true;
+    return fail(CORTEX_ERR_TIMEOUT, std::string(where) + ": a device wait timed out");
+  }
   if (e & kErrBuild) return fail(CORTEX_ERR_CUDA, std::string(where) + ": builder consistency check failed");
   if (e & kErrSegment) return fail(CORTEX_ERR_UNSUPPORTED, std::string(where) + ": a sub-graph segment exceeds the staging capacity");
   if (e & kErrRaster) return fail(CORTEX_ERR_OVERFLOW, std::string(where) + ": raster capacity exceeded");
@@ -202,6 +207,7 @@ StepArgs make_args(cortex_net* h) {
   a.max_depth = h->max_depth;
   a.max_nb = h->max_nb;
   a.timeout_ns = h->timeout_ns;
+  a.withhold_block = h->withhold_block;
   a.t_fixed = -1;
   return a;
 }
@@ -405,6 +411,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   h->steps_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 1000;
   h->use_graph = o.use_graph >= 0;
   if (o.barrier_timeout_ms > 0) h->timeout_ns = (long long)(o.barrier_timeout_ms * 1e6);
+  h->withhold_block = o.test_withhold_block > 0 ? o.test_withhold_block - 1 : -1;
 
   std::vector<int32_t> tb;
   int rc = plan_blocks(h, o, tb);
@@ -583,6 +590,7 @@ int cortex_build(const cortex_params* params, uint64_t seed, const cortex_option
 
 int cortex_simulate(cortex_net* h, int64_t n_steps) {
   if (!h || n_steps < 0) return fail(CORTEX_ERR_ARG, "cortex_simulate: handle / n_steps");
+  if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_simulate: an earlier device wait timed out; free the handle");
   unsigned long long ev_before = 0;
   {
     std::vector<unsigned long long> e(h->n_nets);
@@ -703,7 +711,7 @@ int cortex_constants(cortex_net* h, int32_t net_idx, float* out6, uint32_t* thr,
   if (out6) {
     out6[0] = d.p11;
     out6[1] = d.p21;
-    out6[2] = d.p22;
+    out6[2] = d.p22m1;
     out6[3] = d.w_exc;
     out6[4] = d.w_inh;
     out6[5] = d.j_ext;

@@ -18,6 +18,8 @@ namespace cortex {
 // ---- propagators and Poisson thresholds (FP64, once) ----------------------------------------
 // Exact integration of Eq. 1 with an exponential current (Eq. 3 as a current synapse):
 //   P22 = exp(-h/tau_m), P11 = exp(-h/tau_syn), P21 = tau_m tau_syn / (C (tau_syn - tau_m)) (P11 - P22)
+// The neuron update uses P22 - 1 = expm1(-h/tau_m) (V + ((P22 - 1) V + P21 I)): P22 is within 1% of 1,
+// so P22 itself would carry a float rounding that the stationary potential amplifies by 1/(1 - P22).
 // Poisson(lambda = nu_ext dt) thresholds thr[k] = floor(2^32 P(X <= k)), saturating at 2^32 - 1.
 __global__ void k_props(NetDev* nets, int n_nets) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,7 +31,7 @@ __global__ void k_props(NetDev* nets, int n_nets) {
   const double p21 = tm * ts / (c * (ts - tm)) * (p11 - p22);
   d.p11 = (float)p11;
   d.p21 = (float)p21;
-  d.p22 = (float)p22;
+  d.p22m1 = (float)expm1(-h / tm);
   d.n_ref = (int32_t)llround((double)d.t_ref / h);
   const double lam = (double)d.nu_ext_hz * (double)d.dt / 1000.0;
   double pmf = exp(-lam), cdf = pmf;

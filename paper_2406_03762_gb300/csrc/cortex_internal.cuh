@@ -49,7 +49,7 @@ struct NetDev {
   int32_t wdtype;                              // 0 f32, 1 bf16
   int32_t first_block, n_blocks;               // blocks of this network in the work table
   int32_t n_ref, n_thr;
-  float p11, p21, p22;                         // FP32 propagators (from FP64 on the device)
+  float p11, p21, p22m1;                       // FP32 propagators (from FP64 on the device); P22 - 1
   float v_th, v_reset, j_ext;
   float w_exc, w_inh;                          // stored weights (bf16-rounded when wdtype = 1)
   // host-provided inputs for the propagator kernel
@@ -106,6 +106,7 @@ struct StepArgs {
   int32_t cap_w, cap_m;               // staging bytes per spike: weight stream, meta stream
   int32_t max_nt, max_depth, max_nb;  // shared-memory layout maxima over the blocks
   long long timeout_ns;
+  int32_t withhold_block;             // test hook: this block never publishes (-1: none)
   // delivery-only launches (cortex_deliver): fixed emission step
   long long t_fixed;
 };

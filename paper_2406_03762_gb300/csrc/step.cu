@@ -90,11 +90,11 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
 
 // ---- one neuron, one step (Eq. 1-3, exact integration) --------------------------------------
 //   in = ring cell of this step (cleared); k = Poisson draw; ext = k * J_ext
-//   refractory: V = V_reset, counter - 1;  else V = fma(P22, V, P21 * I) with the old I
+//   refractory: V = V_reset, counter - 1;  else V = V + fma(P22 - 1, V, P21 * I) with the old I
 //   I = fma(P11, I, in); I = I + ext
 //   V >= V_th: spike, V = V_reset, counter = n_ref (Eq. 2)
 struct NeuronConst {
-  float p11, p21, p22, v_th, v_reset, j_ext;
+  float p11, p21, p22m1, v_th, v_reset, j_ext;
   int32_t n_ref, n_thr;
 };
 
@@ -107,7 +107,7 @@ __device__ __forceinline__ bool update_neuron(float& v, float& cur, int32_t& r, 
     v = nd.v_reset;
     r -= 1;
   } else {
-    v = __fmaf_rn(nd.p22, v, __fmul_rn(nd.p21, cur));
+    v = __fadd_rn(v, __fmaf_rn(nd.p22m1, v, __fmul_rn(nd.p21, cur)));
   }
   cur = __fmaf_rn(nd.p11, cur, in);
   cur = __fadd_rn(cur, ext);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
   NeuronConst nd;
   nd.p11 = ndg.p11;
   nd.p21 = ndg.p21;
-  nd.p22 = ndg.p22;
+  nd.p22m1 = ndg.p22m1;
   nd.v_th = ndg.v_th;
   nd.v_reset = ndg.v_reset;
   nd.j_ext = ndg.j_ext;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
         }
         __syncthreads();
       }
-      if (persistent && tid == 0) {
+      if (persistent && tid == 0 && blk != a.withhold_block) {
         // the release store orders every write of the block before it (bar.sync + cumulativity)
         st_release_u64(a.pub_flag + blk, (unsigned long long)(epoch + 1u) | ((unsigned long long)wcnt[kMaxWarps] << 32));
       }

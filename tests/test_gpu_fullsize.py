@@ -1,0 +1,162 @@
+"""GPU path at the benchmark's full sizes, and the precision paths against the FP64 oracle.
+
+A neuron's trajectory is fixed by its own incoming synapses and the spikes their sources emitted
+(Eq. 1-3), so the oracle's replay of a few targets, driven by the GPU's raster of the whole
+network, checks a network far too large for the full oracle one neuron at a time: each sampled
+target's spikes and final (V, I, refractory count) must equal the GPU's bit for bit.  The
+launch configuration is the one the benchmark times (persistent kernel, 1000 steps per launch,
+default warps per block).
+
+Precision (FP32 state and accumulation): potentials within 1e-6 of the FP64 oracle relative to
+max(|V64|, V_th) until the rasters first differ, population rates within 1% (or the 3-sigma band
+of the rate fluctuations) after that.  BF16 weights: rates against the FP64 oracle on the
+10,000-neuron network with the statistics of the 1e6-neuron configuration (K = 11,250)."""
+import numpy as np
+import pytest
+
+from helpers import first_mismatch, oracle_params, oracle_run
+from oracle import oracle as orc
+from paper_2406_03762_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BENCH_OPTS = dict(steps_per_launch=1000)
+
+
+def _targets(spec, n_sample, seed):
+    rng = np.random.default_rng(seed)
+    fixed = [0, spec.n_exc - 1, spec.n_exc, spec.n - 1]
+    return np.unique(np.concatenate([fixed, rng.integers(0, spec.n, n_sample)])).astype(np.int32)
+
+
+def _replay_check(net, spec, seed, steps, net_idx=0, n_sample=40, sample_seed=0):
+    gs, gi = net.spikes(net_idx)
+    gv, gc, gr = net.state(net_idx)
+    tg = _targets(spec, n_sample, sample_seed)
+    ps, pi, (pv, pc, pr) = orc.replay(oracle_params(spec), seed, tg, steps, gs, gi)
+    keep = np.isin(gi, tg)
+    assert np.array_equal(ps, gs[keep]) and np.array_equal(pi, gi[keep]), "spikes of a sampled target differ"
+    assert np.array_equal(pv, gv[tg].astype(np.float64)), "V of a sampled target differs"
+    assert np.array_equal(pc, gc[tg].astype(np.float64)), "I of a sampled target differs"
+    assert np.array_equal(pr, gr[tg]), "refractory count of a sampled target differs"
+    return len(gs), int(keep.sum())
+
+
+@pytest.mark.parametrize("name,steps", [("c1", 1000), ("c2", 1000), ("c3", 500)])
+def test_full_size_sampled_targets_bit_exact(cortex, name, steps):
+    cfg = W.CONFIGS[name]
+    spec, seed = cfg["spec"], cfg["seed"]
+    with cortex.Network(spec, seed, cortex.make_options(**BENCH_OPTS)) as net:
+        st = net.stats()
+        assert st["n_synapses"] == spec.n * spec.k
+        net.simulate(steps)
+        n_spikes, n_sampled = _replay_check(net, spec, seed, steps)
+    assert n_spikes > steps, "the network should be active"
+
+
+@pytest.mark.slow
+def test_c1_raster_bit_exact_over_50ms(cortex):
+    """The whole raster of the 112,500-neuron network against the full FP32 oracle, 500 steps."""
+    cfg = W.CONFIGS["c1"]
+    spec, seed, steps = cfg["spec"], cfg["seed"], 500
+    with cortex.Network(spec, seed, cortex.make_options(**BENCH_OPTS)) as net:
+        net.simulate(steps)
+        gs, gi = net.spikes()
+        gv, gc, gr = net.state()
+        st = net.stats()
+    ref, os_, oi, _ = oracle_run(spec, seed, steps)
+    assert len(os_) > 1000
+    assert first_mismatch(gs, gi, os_, oi) == -1
+    ov, oc, orr = ref.state()
+    assert np.array_equal(gv.astype(np.float64), ov) and np.array_equal(gc.astype(np.float64), oc)
+    assert np.array_equal(gr, orr)
+    assert st["events"] == ref.events
+
+
+def test_batch_64_networks_sampled_targets_bit_exact(cortex):
+    """The 64 uneven networks stepped together for 500 ms; three targets of every instance."""
+    specs, seeds = W.batch_specs()
+    steps = W.CONFIGS["c4"]["steps"]
+    with cortex.Network(specs, seeds, cortex.make_options(**BENCH_OPTS)) as net:
+        assert net.stats()["n_nets"] == 64
+        net.simulate(steps)
+        for b, (spec, seed) in enumerate(zip(specs, seeds)):
+            _replay_check(net, spec, seed, steps, net_idx=b, n_sample=2, sample_seed=b)
+
+
+def _rate_check(spec, s_a, i_a, s_b, i_b, t0, t1, block=250):
+    """Relative error of each population's mean rate over [t0, t1) and the 3-sigma band from
+    block-to-block fluctuations (blocks of `block` steps) of both runs."""
+    out = []
+    for lo, hi in ((0, spec.n_exc), (spec.n_exc, spec.n)):
+        edges = np.arange(t0, t1 + 1, block)
+        def per_block(s, i):
+            m = (i >= lo) & (i < hi)
+            return np.histogram(s[m], bins=edges)[0].astype(np.float64)
+        a, b = per_block(s_a, i_a), per_block(s_b, i_b)
+        mean_b = b.mean()
+        rel = (a.mean() - mean_b) / mean_b
+        sig = np.sqrt(a.var(ddof=1) / len(a) + b.var(ddof=1) / len(b)) / mean_b
+        out.append((rel, sig))
+    return out
+
+
+def test_fp32_potentials_and_rates_against_fp64_oracle(cortex):
+    """N = 2,500: V of every neuron after every step of the first 100 ms within 1e-6 of the FP64
+    oracle (relative to max(|V64|, V_th)) while the rasters agree; rates over 200 ms."""
+    cfg = W.CONFIGS["c0"]
+    spec, seed, steps = cfg["spec"], cfg["seed"], cfg["steps"]
+    n_v = 1000
+    gv = np.zeros((n_v, spec.n), np.float64)
+    with cortex.Network(spec, seed) as net:
+        for t in range(n_v):
+            net.simulate(1)
+            gv[t] = net.state()[0]
+        net.simulate(steps - n_v)
+        gs, gi = net.spikes()
+    ref, os_, oi, tr = oracle_run(spec, seed, steps, precision=orc.FP64,
+                                  trace_ids=np.arange(spec.n, dtype=np.int32))
+    v64 = tr[:n_v]
+    fm = first_mismatch(gs, gi, os_, oi)
+    t_star = int(min(gs[fm], os_[fm])) if 0 <= fm < min(len(gs), len(os_)) else (steps if fm == -1 else int(gs[-1]))
+    t_v = min(t_star, n_v)
+    assert t_v >= 500, f"rasters differ from step {t_star}"
+    err = np.abs(gv[:t_v] - v64[:t_v]) / np.maximum(np.abs(v64[:t_v]), spec.v_th)
+    assert err.max() <= 1e-6, f"max relative V error {err.max():.3g}"
+    if t_star < steps:
+        for rel, sig in _rate_check(spec, gs, gi, os_, oi, t_star, steps):
+            assert abs(rel) <= max(0.01, 3 * sig)
+
+
+def test_bf16_rates_against_fp64_oracle_on_10k_network(cortex):
+    """BF16 weights (J_E 87.8 -> 88, J_I -439 -> -440, +0.23%), FP32 accumulation and state, on
+    N = 10,000 with K = 11,250 (the statistics of the 1e6-neuron configuration): population rates
+    over 500 ms within 2%, or within the 3-sigma band of the rate fluctuations, of the FP64 oracle
+    with the exact weights."""
+    spec = W.NetSpec(8000, 2000, 9000, 2250, weight_dtype=W.BF16)
+    seed, steps = W.CONFIGS["c3"]["seed"], 5000
+    with cortex.Network(spec, seed) as net:
+        net.simulate(steps)
+        gs, gi = net.spikes()
+    _, os_, oi, _ = oracle_run(spec, seed, steps, precision=orc.FP64)
+    n = min(len(gs), len(os_))
+    assert n > 10000
+    for rel, sig in _rate_check(spec, gs, gi, os_, oi, 0, steps):
+        assert abs(rel) <= max(0.02, 3 * sig), f"rate error {rel:.4f} (3 sigma {3 * sig:.4f})"
+
+
+def test_barrier_wait_times_out_with_an_error_status(cortex):
+    """One block never publishes its spikes (test hook), so every block's bounded wait at the
+    window barrier runs out: cortex_simulate returns CORTEX_ERR_TIMEOUT, further calls on the
+    handle return it at once, and the CUDA context stays usable for a new network."""
+    cfg = W.CONFIGS["c0"]
+    spec, seed = cfg["spec"], cfg["seed"]
+    opts = cortex.make_options(test_withhold_block=1, barrier_timeout_ms=100.0, use_graph=-1)
+    with cortex.Network(spec, seed, opts) as net:
+        assert net.simulate_status(20) == -4
+        assert net.simulate_status(20) == -4
+    with cortex.Network(spec, seed) as net:
+        net.simulate(300)
+        gs, gi = net.spikes()
+    _, os_, oi, _ = oracle_run(spec, seed, 300)
+    assert first_mismatch(gs, gi, os_, oi) == -1

@@ -51,7 +51,7 @@ def test_constants_bit_equal(cortex, spec):
         c6, thr, nref = net.constants()
     ref = orc.Network(oracle_params(spec), 1)
     c8, othr, onref = ref.constants_f32()
-    assert c6[0] == c8[0] and c6[1] == c8[1] and c6[2] == c8[2]          # P11, P21, P22
+    assert c6[0] == c8[0] and c6[1] == c8[1] and c6[2] == c8[2]          # P11, P21, P22 - 1
     assert c6[3] == c8[4] and c6[4] == c8[5] and c6[5] == c8[6]          # weights, J_ext
     assert np.array_equal(thr, othr) and nref == onref
 

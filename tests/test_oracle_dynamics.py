@@ -107,3 +107,39 @@ def test_refractory_counter_and_current_keep_evolving():
     p11 = math.exp(-p.dt / TAU_S)
     # step 0: I = P11*100; step 1: I = P11*I + 50 (spike from step 0, delay 1); step 2: decay
     assert np.isclose(cur[1], ((100.0 * p11) * p11 + 50.0) * p11, rtol=1e-14)
+
+
+def test_propagator_p22_minus_one_matches_its_series():
+    """P22 - 1 = e^{-x} - 1, x = h/tau_m, summed as its Taylor series (no expm1 call), and
+    P22 = 1 + (P22 - 1) to rounding; the float value is that number rounded once."""
+    p = o.Params(n_exc=1, n_inh=0, k_exc=0, k_inh=0)
+    p64, p32, _ = o.propagators(p)
+    x = p.dt / p.tau_m
+    series, term = 0.0, 1.0
+    for k in range(1, 12):
+        term *= -x / k
+        series += term
+    assert abs(p64[4] - series) <= 2e-18
+    assert abs((1.0 + p64[4]) - p64[2]) <= 2.3e-16
+    assert p32[4] == np.float32(series)
+
+
+def test_fp32_potentials_track_fp64_within_1e6():
+    """The FP32 update (V + fma(P22 - 1, V, P21 I)) stays within 1e-6 of the FP64 run, relative to
+    max(|V64|, V_th), on the N=2,500 Brunel network over 100 ms while the rasters agree."""
+    from paper_2406_03762_gb300 import workloads as W
+    c0 = W.CONFIGS["c0"]
+    spec, seed = c0["spec"], c0["seed"]
+    runs = []
+    for prec in (o.FP32, o.FP64):
+        d = {k: v for k, v in spec.as_dict().items() if k in o.Params.__dataclass_fields__}
+        net = o.Network(o.Params(precision=prec, **d), seed)
+        tr = net.simulate(1000, trace_ids=np.arange(spec.n, dtype=np.int32))
+        runs.append((tr.reshape(1000, spec.n), *net.raster()))
+    (v32, s32, i32), (v64, s64, i64) = runs
+    n = min(len(s32), len(s64))
+    bad = np.nonzero((s32[:n] != s64[:n]) | (i32[:n] != i64[:n]))[0]
+    t_star = int(s32[bad[0]]) if len(bad) else (1000 if len(s32) == len(s64) else int(s32[n - 1]))
+    assert t_star >= 500
+    err = np.abs(v32[:t_star] - v64[:t_star]) / np.maximum(np.abs(v64[:t_star]), spec.v_th)
+    assert err.max() <= 1e-6

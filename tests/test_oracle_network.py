@@ -177,3 +177,46 @@ def test_simulate_in_chunks_equals_one_run():
     for x, y in zip(a.state(), b.state()):
         assert np.array_equal(x, y)
     assert np.array_equal(a.ring(), b.ring())
+
+
+def _brunel_small(**kw):
+    base = dict(n_exc=800, n_inh=200, k_exc=80, k_inh=20)
+    base.update(kw)
+    return o.Params(**base)
+
+
+@pytest.mark.parametrize("prec,dmin,dmax", [(o.FP32, 1, 16), (o.FP64, 1, 16), (o.FP32, 5, 40)])
+def test_replay_of_targets_reproduces_the_full_simulation(prec, dmin, dmax):
+    """A neuron's trajectory is fixed by its incoming synapses and the raster (Eq. 1-3), so
+    replaying chosen targets against the full run's raster gives their spikes and final state."""
+    p = _brunel_small(precision=prec, d_min=dmin, d_max=dmax)
+    seed, steps = 77, 600
+    net = o.Network(p, seed)
+    net.simulate(steps)
+    rs, ri = net.raster()
+    assert len(rs) > 500
+    v, c, r = net.state()
+    rng = np.random.default_rng(3)
+    tg = np.unique(np.concatenate([[0, 799, 800, 999], rng.integers(0, 1000, 40)]))
+    ps, pi, (pv, pc, pr) = o.replay(p, seed, tg, steps, rs, ri)
+    keep = np.isin(ri, tg)
+    assert np.array_equal(ps, rs[keep]) and np.array_equal(pi, ri[keep])
+    assert np.array_equal(pv, v[tg]) and np.array_equal(pc, c[tg]) and np.array_equal(pr, r[tg])
+
+
+def test_replay_detects_a_missing_presynaptic_spike():
+    """Dropping one raster spike of a source that projects onto a target changes that target's
+    replayed state: the replay really consumes the raster."""
+    p = _brunel_small()
+    seed, steps = 78, 300
+    net = o.Network(p, seed)
+    net.simulate(steps)
+    rs, ri = net.raster()
+    target = 5
+    src, dly = o.incoming(seed, p, target)
+    hit = np.nonzero(np.isin(ri, src) & (rs + dly.max() < steps - 1))[0]
+    assert len(hit) > 0
+    drop = hit[len(hit) // 2]
+    _, _, (v0, c0, _) = o.replay(p, seed, [target], steps, rs, ri)
+    _, _, (v1, c1, _) = o.replay(p, seed, [target], steps, np.delete(rs, drop), np.delete(ri, drop))
+    assert (v0[0], c0[0]) != (v1[0], c1[0])
