@@ -433,8 +433,8 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     d.k = p.k_exc + p.k_inh;
     d.d_min = p.d_min;
     d.d_max = p.d_max;
-    d.depth = p.d_max;
-    d.window = p.d_min;
+    d.depth = p.d_max + 1;   // the persistent window leaves one slot pending across its barrier
+    d.window = p.d_min + 1;  // persistent window (split launches use at most d_min steps)
     d.dbits = 0;
     while ((1 << d.dbits) < p.d_max - p.d_min + 1) ++d.dbits;
     d.seed_lo = (uint32_t)seeds[b];
@@ -489,7 +489,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     h->max_nb = std::max(h->max_nb, nbk);
     h->max_depth = std::max(h->max_depth, d.depth);
     h->w_max = std::max(h->w_max, d.window);
-    h->w_split = std::min(h->w_split, d.window);
+    h->w_split = std::min(h->w_split, d.d_min);
     neuron_base += d.n;
     h->nets_h.push_back(d);
   }

@@ -13,7 +13,7 @@
 //             repeats a cell), then u16 end[w] for the block's delivery warps w = 0..13 (entries of
 //             warps 0..w; unused entries repeat the total).
 //   state     V (f32), I (f32), refractory counter (i32) per neuron.
-//   ring      per block [D][T_b] floats, D = d_max: cell (slot, j) holds the input due at the
+//   ring      per block [D][T_b] floats, D = d_max + 1: cell (slot, j) holds the input due at the
 //             step t with t mod D == slot for local target j.
 //   pub       spike lists published per window: ids[(parity*W_max + ws) * n_total + pub_base + k],
 //             counts[(parity*W_max + ws) * n_blocks + block], mailbox[block] = (windows completed,
@@ -43,7 +43,7 @@ constexpr int kErrBuild = 8;
 
 struct NetDev {
   int32_t n, n_exc, n_inh, k_exc, k_inh, k;
-  int32_t d_min, d_max, depth, window;        // depth D = d_max, window W = d_min
+  int32_t d_min, d_max, depth, window;        // depth D = d_max + 1, window W = d_min + 1
   int32_t dbits;                               // bits of (delay - d_min) in a record's meta
   uint32_t seed_lo, seed_hi;
   int32_t wdtype;                              // 0 f32, 1 bf16

@@ -10,10 +10,17 @@
 // lane order.  So every cell receives its weights in the order (emission step, source id, draw
 // index) with no atomics and no locks (Eq. 12-14).
 //
-// One step (Sec. II-B): update all owned neurons (consuming the ring slot of this step), compact
-// the spikes into the block's ascending list, publish it; every W = d_min steps (the window) the
-// blocks of a network meet at a barrier and deliver the window's spikes, which land at least d_min
-// steps later and so never in a slot the window still reads.
+// One step (Sec. II-B, Eq. 1-3) has two halves.  The V half updates the membrane potential from
+// V and I of the previous step, applies the refractory clamp and the threshold: it decides the
+// step's spikes.  The I half decays I and adds the ring slot of the step and the Poisson drive.
+// A spike emitted at step t arrives at slot t + d (d >= d_min) and so first changes I at t + d and
+// a spike decision at t + d + 1.  The persistent kernel therefore runs windows of W = d_min + 1
+// steps between grid barriers: inside a window every V half and every I half but the last only
+// read slots that earlier windows completed, and the last step's I half waits until the window's
+// spikes have been delivered (it runs at the start of the next window, or in the epilogue).  The
+// blocks of a network meet at one barrier per window, publish the window's spikes and deliver
+// them; the ring has D = d_max + 1 slots so that no delivery reaches the pending slot.  Launches
+// without the barrier (split mode) run whole steps, at most d_min per window.
 //
 // Delivery runs in rounds of up to kSpikeBatch spikes.  All warps stage the record segments of
 // round r + kStages - 1 into shared memory with 16-byte cp.async copies (each spike has a
@@ -89,34 +96,36 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
 }
 
 // ---- one neuron, one step (Eq. 1-3, exact integration) --------------------------------------
-//   in = ring cell of this step (cleared); k = Poisson draw; ext = k * J_ext
-//   refractory: V = V_reset, counter - 1;  else V = V + fma(P22 - 1, V, P21 * I) with the old I
-//   I = fma(P11, I, in); I = I + ext
-//   V >= V_th: spike, V = V_reset, counter = n_ref (Eq. 2)
+//   V half: refractory: V = V_reset, counter - 1;  else V = V + fma(P22 - 1, V, P21 * I) with
+//           the I of the previous step;  V >= V_th: spike, V = V_reset, counter = n_ref (Eq. 2)
+//   I half: in = ring cell of the step (cleared); k = Poisson draw; ext = k * J_ext;
+//           I = fma(P11, I, in); I = I + ext
 struct NeuronConst {
   float p11, p21, p22m1, v_th, v_reset, j_ext;
   int32_t n_ref, n_thr;
 };
 
-__device__ __forceinline__ bool update_neuron(float& v, float& cur, int32_t& r, float in, uint32_t u,
-                                              const NeuronConst& nd, const uint32_t* thr) {
-  int k = 0;
-  while (k < nd.n_thr - 1 && u >= thr[k]) ++k;
-  const float ext = __fmul_rn((float)k, nd.j_ext);
+__device__ __forceinline__ bool v_half(float& v, float cur, int32_t& r, const NeuronConst& nd) {
   if (r > 0) {
     v = nd.v_reset;
     r -= 1;
   } else {
     v = __fadd_rn(v, __fmaf_rn(nd.p22m1, v, __fmul_rn(nd.p21, cur)));
   }
-  cur = __fmaf_rn(nd.p11, cur, in);
-  cur = __fadd_rn(cur, ext);
   const bool spk = v >= nd.v_th;
   if (spk) {
     v = nd.v_reset;
     r = nd.n_ref;
   }
   return spk;
+}
+
+__device__ __forceinline__ void i_half(float& cur, float in, uint32_t u, const NeuronConst& nd, const uint32_t* thr) {
+  int k = 0;
+  while (k < nd.n_thr - 1 && u >= thr[k]) ++k;
+  const float ext = __fmul_rn((float)k, nd.j_ext);
+  cur = __fmaf_rn(nd.p11, cur, in);
+  cur = __fadd_rn(cur, ext);
 }
 
 // Add the weights of one 32-lane chunk to their ring cells (key = cell, 0xffffffff = no entry).
@@ -229,6 +238,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
   bool aborted = false;
   __syncthreads();
 
+  const bool defer = persistent;  // V/I halves with the window's last I half after the barrier
+  bool pend = false;               // the I half of the previous window's last step is due
   const int W = persistent ? window : min(window, a.n_steps);
   const int tw_u = (nt + n_warps - 1) / n_warps;  // update split over the warps
   int done = 0;
@@ -243,25 +254,38 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
       for (int ws = 0; ws < Wn; ++ws) {
         const long long t = t0 + ws;
         const int slot = (tm0 + ws) % D;
-        float* rs = ring + (int64_t)slot * nt;
+        const int pslot = (tm0 + ws + D - 1) % D;    // slot of step t - 1
+        const bool prev = defer && (ws > 0 || pend);  // the I half of step t - 1 is still due
+        float* rs = ring + (int64_t)(defer ? pslot : slot) * nt;
+        const uint32_t tu = (uint32_t)(defer ? t - 1 : t);
         const int lo = warp * tw_u, hi = min(lo + tw_u, nt);
         uint32_t cw = 0;
         for (int c = lo; c < hi; c += 32) {
           const int j = c + lane;
           bool spk = false;
           if (j < hi) {
-            const float in = rs[j];
-            rs[j] = 0.0f;
-            const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)t, kStreamPoisson, 0u),
-                                           seed_lo, seed_hi);
             float v = sV[j], cur = sI[j];
             int32_t r = sR[j];
-            spk = update_neuron(v, cur, r, in, rr.x, nd, thr);
+            if (defer) {
+              if (prev) {
+                const float in = rs[j];
+                rs[j] = 0.0f;
+                const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+                i_half(cur, in, rr.x, nd, thr);
+              }
+              spk = v_half(v, cur, r, nd);
+            } else {
+              const float in = rs[j];
+              rs[j] = 0.0f;
+              const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+              spk = v_half(v, cur, r, nd);
+              i_half(cur, in, rr.x, nd, thr);
+            }
             sV[j] = v;
             sI[j] = cur;
             sR[j] = r;
           }
-          const uint32_t bal = __ballot_sync(0xffffffffu, spk);
+        const uint32_t bal = __ballot_sync(0xffffffffu, spk);
           if (spk) wlist[lo + cw + __popc(bal & lanemask_lt())] = (uint32_t)(wk.t0 + j);
           cw += __popc(bal);
         }
@@ -281,6 +305,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
         }
         __syncthreads();
       }
+      pend = defer;
       if (persistent && tid == 0 && blk != a.withhold_block) {
         // the release store orders every write of the block before it (bar.sync + cumulativity)
         st_release_u64(a.pub_flag + blk, (unsigned long long)(epoch + 1u) | ((unsigned long long)wcnt[kMaxWarps] << 32));
@@ -561,8 +586,21 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
     done += Wn;
   }
 
-  // ---- epilogue: write back state and ring, counters ----
+  // ---- epilogue: the pending I half of the last step, then write back state and ring ----
   __syncthreads();
+  if (pend && !aborted) {
+    const long long tl = t_start + a.n_steps - 1;
+    float* rs = ring + (int64_t)(tl % D) * nt;
+    for (int j = tid; j < nt; j += blockDim.x) {
+      const float in = rs[j];
+      rs[j] = 0.0f;
+      const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)tl, kStreamPoisson, 0u), seed_lo, seed_hi);
+      float cur = sI[j];
+      i_half(cur, in, rr.x, nd, thr);
+      sI[j] = cur;
+    }
+    __syncthreads();
+  }
   if (do_update) {
     for (int j = tid; j < nt; j += blockDim.x) {
       a.V[nbase + j] = sV[j];

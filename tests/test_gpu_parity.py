@@ -122,7 +122,7 @@ def test_raster_c0_bit_exact(cortex, opts):
 
 
 def test_raster_deep_delays_window(cortex):
-    """d = 5..40: five steps per barrier window, ring depth 40."""
+    """d = 5..40: six steps per barrier window (d_min + 1), ring depth 41."""
     spec, seed, steps = SPECS[1], 2024, 1500
     for opts in (dict(), dict(mode=1)):
         with cortex.Network(spec, seed, cortex.make_options(**opts)) as net:
