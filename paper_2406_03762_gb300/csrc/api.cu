@@ -60,6 +60,7 @@ struct cortex_net {
   uint32_t* pub_ids = nullptr;
   uint32_t* pub_cnt = nullptr;
   unsigned long long* pub_flag = nullptr;
+  unsigned long long* mbox = nullptr;
   int32_t* raster_step = nullptr;
   int32_t* raster_id = nullptr;
   unsigned long long* raster_count = nullptr;
@@ -193,6 +194,7 @@ StepArgs make_args(cortex_net* h) {
   a.pub_ids = h->pub_ids;
   a.pub_cnt = h->pub_cnt;
   a.pub_flag = h->pub_flag;
+  a.mbox = h->mbox;
   a.raster_step = h->raster_step;
   a.raster_id = h->raster_id;
   a.raster_count = h->raster_count;
@@ -207,6 +209,7 @@ StepArgs make_args(cortex_net* h) {
   a.max_depth = h->max_depth;
   a.max_nb = h->max_nb;
   a.timeout_ns = h->timeout_ns;
+  a.bf16 = h->wdtype == CORTEX_BF16 ? 1 : 0;
   a.withhold_block = h->withhold_block;
   a.t_fixed = -1;
   return a;
@@ -528,6 +531,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(h->alloc(&h->pub_ids, 4 * (size_t)2 * h->w_max * h->n_total), "alloc spike lists");
   TRY(h->alloc(&h->pub_cnt, 4 * (size_t)2 * h->w_max * h->n_blocks), "alloc spike counts");
   TRY(h->alloc(&h->pub_flag, 8 * (size_t)h->n_blocks), "alloc flags");
+  TRY(h->alloc(&h->mbox, 8 * 2 * (size_t)kMboxWords * h->n_blocks), "alloc mailboxes");
   TRY(h->alloc(&h->raster_step, 4 * h->total_raster), "alloc raster");
   TRY(h->alloc(&h->raster_id, 4 * h->total_raster), "alloc raster");
   TRY(h->alloc(&h->raster_count, 8 * (size_t)n_nets), "alloc counters");
@@ -555,6 +559,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   }
   TRY(cudaMemsetAsync(h->ring, 0, 4 * h->total_ring, s), "memset ring");
   TRY(cudaMemsetAsync(h->pub_flag, 0, 8 * (size_t)h->n_blocks, s), "memset flags");
+  TRY(cudaMemsetAsync(h->mbox, 0, 8 * 2 * (size_t)kMboxWords * h->n_blocks, s), "memset mailboxes");
   TRY(cudaMemsetAsync(h->pub_cnt, 0, 4 * (size_t)2 * h->w_max * h->n_blocks, s), "memset counts");
   TRY(cudaMemsetAsync(h->raster_count, 0, 8 * (size_t)n_nets, s), "memset");
   TRY(cudaMemsetAsync(h->events, 0, 8 * (size_t)n_nets, s), "memset");

@@ -29,7 +29,11 @@ constexpr int kPoissonCap = 64;     // Poisson threshold table entries
 constexpr int kMaxWarps = 14;       // warps per block, all of them delivery warps (32-byte header: 4 + 2 * 14)
 constexpr int kSpikeBatch = 32;     // spikes staged per delivery round (at most)
 constexpr int kStages = 4;          // delivery rounds in flight per block
+constexpr int kHdrAhead = 2 * kStages - 1;        // headers are fetched this many rounds ahead
+constexpr int kHdrSlots = kHdrAhead - kStages + 1;  // rounds of headers held in shared memory
 constexpr int kIdCap = 2048;        // spike ids of a window kept in shared memory
+constexpr int kMboxWords = 16;      // 64-bit words of a block's mailbox line (128 bytes)
+constexpr int kInlMax = 3 * (kMboxWords - 1);  // spike ids a mailbox line carries (one count word)
 
 constexpr uint32_t kStreamConn = 1u;
 constexpr uint32_t kStreamV0 = 2u;
@@ -91,7 +95,8 @@ struct StepArgs {
   float* ring;
   uint32_t* pub_ids;
   uint32_t* pub_cnt;
-  unsigned long long* pub_flag;   // mailbox per block: windows completed | count of ws 0 << 32
+  unsigned long long* pub_flag;   // per block: windows completed (kept across launches)
+  unsigned long long* mbox;       // [2][n_blocks][kMboxWords] self-tagged mailbox lines
   int32_t* raster_step;
   int32_t* raster_id;
   unsigned long long* raster_count;   // per network: spikes emitted so far
@@ -101,6 +106,7 @@ struct StepArgs {
   int32_t n_steps;                    // steps this launch
   int32_t phases;                     // kPhaseUpdate | kPhaseDeliver
   int32_t ring_smem;                  // 1: ring slice in shared memory
+  int32_t bf16;                       // 1: weights stored as bf16 (all networks of a handle)
   int32_t stage_bytes;                // shared staging capacity for record segments
   int32_t batch;                      // spikes per delivery round
   int32_t cap_w, cap_m;               // staging bytes per spike: weight stream, meta stream
@@ -159,6 +165,21 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// bring [p, p + bytes) into L2 (p and bytes multiples of 16), no completion tracking
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -211,6 +232,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // 16-byte asynchronous copy global -> shared (L2 only), tracked per thread
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// 8-byte asynchronous copy global -> shared (through L1), tracked per thread
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }

@@ -30,15 +30,8 @@
 
 namespace cortex {
 
-struct SpikeInfo {    // one staged spike of a delivery round
-  uint32_t woff;     // staging byte offset of record 0 of the block's piece, weight stream
-  uint32_t moff;     // ... meta stream
-  uint32_t endw[7];  // header words 1..7: u16 end[w] of the delivery warps
-  uint32_t tm;       // emission step mod D
-};
-
 struct SmemLayout {
-  uint32_t ring, sv, si, sr, thr, cnt, woffs, wcnt, wlist, ids, hdr, rowb, info, perm, tags, stage, total;
+  uint32_t ring, sv, si, sr, thr, cnt, woffs, wcnt, wlist, ids, mbl, mbi, mbc, pk, hdr, desc, perm, tags, stage, total;
 };
 
 __host__ __device__ inline uint32_t align_to(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -77,12 +70,18 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   o = align_to(o, 16);
   L.ids = o;
   o += kIdCap * 4;
-  L.hdr = o;
-  o += (kStages + 1) * kSpikeBatch * 32;
-  L.rowb = o;
-  o += (kStages + 1) * kSpikeBatch * 8;
-  L.info = o;
-  o += kStages * kSpikeBatch * (uint32_t)sizeof(SpikeInfo);
+  L.mbl = o;   // mailbox lines read at the barrier: one per block of the network
+  o += (uint32_t)(max_nb * kMboxWords * 8);
+  L.mbi = o;   // the block's first spike ids of the window (local, u16), for its mailbox line
+  o += align_to(kInlMax * 2, 16);
+  L.mbc = o;   // the block's spike count of every step of the window
+  o += align_to((uint32_t)(w_max * 4), 16);
+  L.pk = o;    // Poisson counts of the window's I halves, [step][target] (persistent kernel)
+  o += align_to((uint32_t)(w_max * max_nt), 16);
+  L.hdr = o;   // fetched headers: kHdrSlots rounds of (32-byte header, 8-byte row start, pad) per spike
+  o += kHdrSlots * kSpikeBatch * 48;
+  L.desc = o;  // piece descriptors: kStages + 1 rounds of 64 bytes per spike
+  o += (kStages + 1) * kSpikeBatch * 64;
   L.perm = o;
   o += kMaxWarps * 32;
   o = align_to(o, 16);
@@ -120,12 +119,21 @@ __device__ __forceinline__ bool v_half(float& v, float cur, int32_t& r, const Ne
   return spk;
 }
 
-__device__ __forceinline__ void i_half(float& cur, float in, uint32_t u, const NeuronConst& nd, const uint32_t* thr) {
+// Poisson count of the external drive by inversion: the smallest k with u < thr[k]
+__device__ __forceinline__ int poisson_k(uint32_t u, const NeuronConst& nd, const uint32_t* thr) {
   int k = 0;
   while (k < nd.n_thr - 1 && u >= thr[k]) ++k;
+  return k;
+}
+
+__device__ __forceinline__ void i_half_k(float& cur, float in, int k, const NeuronConst& nd) {
   const float ext = __fmul_rn((float)k, nd.j_ext);
   cur = __fmaf_rn(nd.p11, cur, in);
   cur = __fadd_rn(cur, ext);
+}
+
+__device__ __forceinline__ void i_half(float& cur, float in, uint32_t u, const NeuronConst& nd, const uint32_t* thr) {
+  i_half_k(cur, in, poisson_k(u, nd, thr), nd);
 }
 
 // Add the weights of one 32-lane chunk to their ring cells (key = cell, 0xffffffff = no entry).
@@ -165,8 +173,9 @@ __device__ __forceinline__ void fold_chunk(float* ring, uint8_t* wtags, uint32_t
 // a barrier per window inside one cooperative launch of n_steps steps).  kRingSmem: the block's
 // ring slice lives in shared memory for the whole launch (loaded in the prologue, written back
 // in the epilogue); otherwise it is updated in place in global memory.
-template <bool kRingSmem>
-__global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
+template <bool kRingSmem, bool kBf16>
+__global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
+  constexpr uint32_t kWsz = kBf16 ? 2u : 4u;  // bytes per stored weight
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
   const int blk = blockIdx.x;
@@ -193,8 +202,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
   const bool persistent = (a.phases & kPhaseBarrier) != 0;
   const bool do_update = (a.phases & kPhaseUpdate) != 0;
   const bool do_deliver = (a.phases & kPhaseDeliver) != 0;
-  const bool bf16 = ndg.wdtype == 1;
-  const uint32_t wsz = bf16 ? 2u : 4u;
   const uint32_t B = (uint32_t)a.batch, cap_w = (uint32_t)a.cap_w, cap = (uint32_t)(a.cap_w + a.cap_m);
 
   const SmemLayout L = make_layout(a.max_nt, a.max_depth, a.w_max, a.max_nb, kRingSmem, a.stage_bytes);
@@ -208,9 +215,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
   uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + L.wcnt);
   uint32_t* wlist = reinterpret_cast<uint32_t*>(smem + L.wlist);
   uint32_t* ids_s = reinterpret_cast<uint32_t*>(smem + L.ids);
-  uint4* hdr_s = reinterpret_cast<uint4*>(smem + L.hdr);
-  unsigned long long* rowb_s = reinterpret_cast<unsigned long long*>(smem + L.rowb);
-  SpikeInfo* info = reinterpret_cast<SpikeInfo*>(smem + L.info);
+  unsigned long long* mbl = reinterpret_cast<unsigned long long*>(smem + L.mbl);
+  uint16_t* mbi = reinterpret_cast<uint16_t*>(smem + L.mbi);
+  uint32_t* mbc = reinterpret_cast<uint32_t*>(smem + L.mbc);
+  uint8_t* pk = smem + L.pk;
+  unsigned char* hdr_s = smem + L.hdr;
+  uint4* desc_s = reinterpret_cast<uint4*>(smem + L.desc);
   uint8_t* perm = smem + L.perm + warp * 32;
   uint8_t* tags = smem + L.tags;
   unsigned char* stage = smem + L.stage;
@@ -238,9 +248,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
   bool aborted = false;
   __syncthreads();
 
+  // Poisson counts of steps tfirst .. tfirst + ns - 1 for every owned target (elements q0, q0 + dq, ...)
+  auto poisson_fill = [&](long long tfirst, int ns, int q0, int dq) {
+    for (int q = q0; q < ns * nt; q += dq) {
+      const int sidx = q / nt, j = q - sidx * nt;
+      const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)(tfirst + sidx), kStreamPoisson, 0u),
+                                     seed_lo, seed_hi);
+      pk[sidx * nt + j] = (uint8_t)poisson_k(rr.x, nd, thr);
+    }
+  };
   const bool defer = persistent;  // V/I halves with the window's last I half after the barrier
   bool pend = false;               // the I half of the previous window's last step is due
   const int W = persistent ? window : min(window, a.n_steps);
+  if (persistent && do_update) {
+    // the first window's table: pk[s] holds step t_start - 1 + s (the I half run before V half s)
+    poisson_fill(t_start - 1, min(W, a.n_steps), tid, blockDim.x);
+    __syncthreads();
+  }
   const int tw_u = (nt + n_warps - 1) / n_warps;  // update split over the warps
   int done = 0;
   while (done < a.n_steps) {
@@ -248,9 +272,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
     const long long t0 = t_start + done;
     const int tm0 = (int)(t0 % D);  // ring slot of the window's first step
     const uint32_t par = persistent ? ((epoch + 1u) & 1u) : 0u;
+    const int n_cw = (Wn + 2) / 3;                          // count words of a mailbox line
+    const uint32_t inl = (uint32_t)(3 * (kMboxWords - n_cw));  // ids a mailbox line carries
 
     // ================= update + compaction + publication =================
     if (do_update) {
+      uint32_t win_total = 0;  // spikes of the block so far in this window
       for (int ws = 0; ws < Wn; ++ws) {
         const long long t = t0 + ws;
         const int slot = (tm0 + ws) % D;
@@ -270,8 +297,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
               if (prev) {
                 const float in = rs[j];
                 rs[j] = 0.0f;
-                const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
-                i_half(cur, in, rr.x, nd, thr);
+                i_half_k(cur, in, pk[ws * nt + j], nd);
               }
               spk = v_half(v, cur, r, nd);
             } else {
@@ -298,40 +324,126 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
           total += x;
         }
         uint32_t* dst = a.pub_ids + ((int64_t)(par * a.w_max + ws) * a.n_total + neuron_base + wk.t0);
-        for (uint32_t q = lane; q < cw; q += 32) dst[before + q] = wlist[lo + q];
+        for (uint32_t q = lane; q < cw; q += 32) {
+          const uint32_t id = wlist[lo + q];
+          dst[before + q] = id;
+          const uint32_t pw = win_total + before + q;
+          if (persistent && pw < inl) mbi[pw] = (uint16_t)(id - (uint32_t)wk.t0);
+        }
         if (tid == 0) {
           a.pub_cnt[(int64_t)(par * a.w_max + ws) * a.n_blocks + blk] = total;
-          if (ws == 0) wcnt[kMaxWarps] = total;
+          mbc[ws] = total;
         }
+        win_total += total;
         __syncthreads();
       }
       pend = defer;
-      if (persistent && tid == 0 && blk != a.withhold_block) {
-        // the release store orders every write of the block before it (bar.sync + cumulativity)
-        st_release_u64(a.pub_flag + blk, (unsigned long long)(epoch + 1u) | ((unsigned long long)wcnt[kMaxWarps] << 32));
+      if (persistent) {
+        // Publication: the block's mailbox line for this window.  Every 64-bit word carries the
+        // window's tag in its top 16 bits, so a reader that sees the tag in a word sees that word's
+        // payload: count words (three u16 step counts each), then id words (three u16 local ids
+        // each).  The fence orders the global id lists (read by others only beyond the line's
+        // capacity) before the words.
+        const unsigned long long tag = (unsigned long long)(((epoch + 1u) & 0x7fffu) | 0x8000u) << 48;
+        const uint32_t nin = min(win_total, inl);
+        if (tid < kMboxWords && blk != a.withhold_block) {
+          unsigned long long pay = 0;
+          for (int f = 0; f < 3; ++f) {
+            if (tid < n_cw) {
+              const int ws = 3 * tid + f;
+              if (ws < Wn) pay |= (unsigned long long)mbc[ws] << (16 * f);
+            } else {
+              const uint32_t pq = 3u * (uint32_t)(tid - n_cw) + (uint32_t)f;
+              if (pq < nin) pay |= (unsigned long long)mbi[pq] << (16 * f);
+            }
+          }
+          __threadfence();
+          st_relaxed_u64(a.mbox + ((size_t)par * a.n_blocks + blk) * kMboxWords + tid, tag | pay);
+        }
+        // L2 prefetch of the spiking rows (every block of the network reads them after the
+        // barrier): the header row and the record rows of the window's first spikes
+        const int pq = tid - (int)(blockDim.x - kInlMax);
+        if (pq >= 0 && (uint32_t)pq < nin) {
+          const uint32_t id = (uint32_t)wk.t0 + mbi[pq];
+          prefetch_l2_bulk(a.hdr + 2 * (hdr_net + (int64_t)id * nb), (uint32_t)nb * 32u);
+          if ((int)id + 1 < ndg.n) {
+            const unsigned long long r0 = (unsigned long long)rec_net + __ldg(a.row_base + row_off + id);
+            const unsigned long long r1 = (unsigned long long)rec_net + __ldg(a.row_base + row_off + id + 1);
+            const unsigned long long spans[2][2] = {{r0 * kWsz, r1 * kWsz}, {r0 * 2ull, r1 * 2ull}};
+            const unsigned char* bases[2] = {reinterpret_cast<const unsigned char*>(a.rec_w),
+                                             reinterpret_cast<const unsigned char*>(a.rec_meta)};
+            for (int st = 0; st < 2; ++st) {
+              unsigned long long b0 = spans[st][0] & ~15ull;
+              const unsigned long long b1 = (spans[st][1] + 15ull) & ~15ull;
+              while (b0 < b1) {
+                const uint32_t len = (uint32_t)min(b1 - b0, 16384ull);
+                prefetch_l2_bulk(bases[st] + b0, len);
+                b0 += len;
+              }
+            }
+          }
+        }
       }
     }
 
     // ================= grid barrier among the blocks of this network =================
+    // Each block of the network has published its line; reading every line with this window's
+    // tag in every needed word is the barrier, and gives the counts and the first spike ids.
     if (persistent) {
       epoch += 1u;
+      const unsigned long long want = (unsigned long long)((epoch & 0x7fffu) | 0x8000u);
       int fail = 0;
-      for (int b = tid; b < nb; b += blockDim.x) {
-        const unsigned long long* f = a.pub_flag + first_block + b;
-        unsigned long long m = ld_acquire_u64(f);
-        if ((int32_t)((uint32_t)m - epoch) < 0) {
-          const long long tb0 = global_ns();
-          uint32_t spins = 0;
-          do {
-            if ((++spins & 255u) == 0 &&
-                (global_ns() - tb0 > a.timeout_ns || *(volatile int32_t*)a.err != 0)) {
-              fail = 1;
-              break;
-            }
-            m = ld_acquire_u64(f);
-          } while ((int32_t)((uint32_t)m - epoch) < 0);
+      auto poll = [&](const unsigned long long* p, unsigned long long w) -> unsigned long long {
+        if ((w >> 48) == want) return w;
+        const long long tb0 = global_ns();
+        uint32_t spins = 0;
+        do {
+          if ((++spins & 255u) == 0 && (global_ns() - tb0 > a.timeout_ns || *(volatile int32_t*)a.err != 0)) {
+            fail = 1;
+            return 0ull;
+          }
+          w = ld_relaxed_u64(p);
+        } while ((w >> 48) != want);
+        return w;
+      };
+      for (int b = tid; b < nb && !fail; b += blockDim.x) {
+        const unsigned long long* line = a.mbox + ((size_t)par * a.n_blocks + first_block + b) * kMboxWords;
+        unsigned long long* ml = mbl + (size_t)b * kMboxWords;
+        unsigned long long w[kMboxWords];
+#pragma unroll
+        for (int j = 0; j < kMboxWords; ++j)  // count words and the first id word, loads in flight together
+          if (j <= n_cw) w[j] = ld_relaxed_u64(line + j);
+        uint32_t tot = 0;
+#pragma unroll
+        for (int j = 0; j < kMboxWords; ++j) {
+          if (j <= n_cw && !fail) {
+            w[j] = poll(line + j, w[j]);
+            ml[j] = w[j];
+            if (j < n_cw)
+              for (int f = 0; f < 3; ++f) {
+                const int ws = 3 * j + f;
+                if (ws < Wn) {
+                  const uint32_t c = (uint32_t)(w[j] >> (16 * f)) & 0xffffu;
+                  cnt_s[ws * nb + b] = c;
+                  tot += c;
+                }
+              }
+          }
         }
-        cnt_s[b] = (uint32_t)(m >> 32);  // count of the window's first step
+        const int n_idw = (int)((min(tot, inl) + 2u) / 3u);
+        for (int j = n_cw + 1; j < n_cw + n_idw && !fail; ++j) ml[j] = poll(line + j, ld_relaxed_u64(line + j));
+        if (tot > inl) __threadfence();  // the block's further ids are read from its global list
+      }
+      // the next window's Poisson table (its first entry is this window's last step, whose I half
+      // runs after the delivery): threads that do not poll fill it meanwhile
+      if (do_update) {
+        const int wn_next = min(W, a.n_steps - done - Wn);
+        const int ns = max(wn_next, 1);
+        if ((int)blockDim.x > nb) {
+          if (tid >= nb) poisson_fill(t0 + Wn - 1, ns, tid - nb, (int)blockDim.x - nb);
+        } else {
+          poisson_fill(t0 + Wn - 1, ns, tid, blockDim.x);
+        }
       }
       if (__syncthreads_or(fail)) {
         if (tid == 0) atomicOr(a.err, kErrTimeout);
@@ -342,55 +454,74 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
 
     // ================= delivery =================
     if (do_deliver) {
-      // counts of every block of this network, then exclusive prefixes per window step
-      for (int q = tid; q < Wn * nb; q += blockDim.x) {
-        const int ws = q / nb, b = q % nb;
-        if (!persistent || ws > 0)
-          cnt_s[ws * (nb + 1) + b] =
-              __ldcg(a.pub_cnt + (int64_t)(par * a.w_max + ws) * a.n_blocks + first_block + b);
-      }
+      // counts of every (window step, block) of this network, flat (step-major), turned in place
+      // into exclusive prefixes: cnt_s[ws * nb + b] = window position of block b's first spike of
+      // step ws; cnt_s[Wn * nb] = spikes of the window
+      const int E = Wn * nb;
+      if (!persistent)
+        for (int q = tid; q < E; q += blockDim.x)
+          cnt_s[q] = __ldcg(a.pub_cnt + (int64_t)(par * a.w_max + q / nb) * a.n_blocks + first_block + q % nb);
       __syncthreads();
-      for (int ws = warp; ws < Wn; ws += n_warps) {
-        uint32_t* c = cnt_s + ws * (nb + 1);
-        uint32_t carry = 0;
-        for (int b0 = 0; b0 < nb; b0 += 32) {
-          const int b = b0 + lane;
-          const uint32_t v = (b < nb) ? c[b] : 0u;
-          uint32_t x = v;
+      {
+        const int per = (E + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int e0 = min(tid * per, E), e1 = min(e0 + per, E);
+        uint32_t loc = 0;
+        for (int e = e0; e < e1; ++e) loc += cnt_s[e];
+        uint32_t x = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) wcnt[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+          uint32_t v = (lane < n_warps) ? wcnt[lane] : 0u;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
           }
-          if (b < nb) c[b] = carry + x - v;
-          carry += __shfl_sync(0xffffffffu, x, 31);
+          if (lane < n_warps) wcnt[lane] = v;
         }
-        if (lane == 0) c[nb] = carry;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        uint32_t o = 0;
-        for (int ws = 0; ws < Wn; ++ws) {
-          woffs[ws] = o;
-          o += cnt_s[ws * (nb + 1) + nb];
+        __syncthreads();
+        uint32_t run = (warp ? wcnt[warp - 1] : 0u) + x - loc;
+        for (int e = e0; e < e1; ++e) {
+          const uint32_t c = cnt_s[e];
+          cnt_s[e] = run;
+          run += c;
         }
-        woffs[Wn] = o;
+        if (tid == 0) cnt_s[E] = wcnt[n_warps - 1];
+        __syncthreads();
+        for (int ws = tid; ws <= Wn; ws += blockDim.x) woffs[ws] = cnt_s[ws * nb];
+        __syncthreads();
       }
-      __syncthreads();
       const uint32_t S_tot = woffs[Wn];
-      // spike ids of the window into shared memory (window order: step, then id); raster
-      for (int task = warp; task < Wn * nb; task += n_warps) {
-        const int ws = task / nb, b = task % nb;
-        const uint32_t* pref = cnt_s + ws * (nb + 1);
-        const uint32_t c = pref[b + 1] - pref[b];
+      if (persistent && S_tot > (uint32_t)kIdCap) {
+        // ids beyond the shared list are read from the global lists: order them after the lines
+        if (tid < nb) __threadfence();
+        __syncthreads();
+      }
+      // spike ids of the window into shared memory (window order: step, then id); raster.  One
+      // thread per (window step, block): the ids come from the block's mailbox line (persistent
+      // kernel, first ids of its window) or from its global list
+      for (int e = tid; e < E; e += blockDim.x) {
+        const uint32_t o = cnt_s[e], c = cnt_s[e + 1] - o;
         if (c == 0) continue;
+        const int ws = e / nb, b = e - ws * nb;
         const uint32_t* src = a.pub_ids + (int64_t)(par * a.w_max + ws) * a.n_total + neuron_base + (int64_t)b * tb_full;
-        const uint32_t o = woffs[ws] + pref[b];
         const bool mine = (b == wk.group) && a.raster_step != nullptr;
-        for (uint32_t q = lane; q < c; q += 32) {
+        uint32_t p0 = 0;  // position of the step's first id in block b's list for the window
+        if (persistent)
+          for (int w2 = 0; w2 < ws; ++w2) p0 += cnt_s[w2 * nb + b + 1] - cnt_s[w2 * nb + b];
+        const unsigned long long* ml = mbl + (size_t)b * kMboxWords + n_cw;
+        for (uint32_t q = 0; q < c; ++q) {
           const bool need = (o + q < (uint32_t)kIdCap) || mine;
-          if (!need) continue;
-          const uint32_t id = __ldcg(src + q);
+          if (!need) break;
+          const uint32_t pw = p0 + q;
+          const uint32_t id = (persistent && pw < inl)
+                                  ? (uint32_t)b * (uint32_t)tb_full + ((uint32_t)(ml[pw / 3u] >> (16u * (pw % 3u))) & 0xffffu)
+                                  : __ldcg(src + q);
           if (o + q < (uint32_t)kIdCap) ids_s[o + q] = id;
           if (mine) {
             const unsigned long long pos = raster_total + o + q;
@@ -410,80 +541,97 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
       // spike id of window index g (shared list, or the published global lists beyond it)
       auto spike_id = [&](uint32_t g) -> uint32_t {
         if (g < (uint32_t)kIdCap) return ids_s[g];
-        int ws = 0;
-        while (ws + 1 < Wn && woffs[ws + 1] <= g) ++ws;
-        const uint32_t* pref = cnt_s + ws * (nb + 1);
-        const uint32_t qq = g - woffs[ws];
-        int lo2 = 0, hi2 = nb;
+        int lo2 = 0, hi2 = E;  // the last (step, block) whose first window position is <= g
         while (hi2 - lo2 > 1) {
           const int mid = (lo2 + hi2) >> 1;
-          if (pref[mid] <= qq) lo2 = mid;
+          if (cnt_s[mid] <= g) lo2 = mid;
           else hi2 = mid;
         }
-        return __ldcg(a.pub_ids + (int64_t)(par * a.w_max + ws) * a.n_total + neuron_base + (int64_t)lo2 * tb_full +
-                      (qq - pref[lo2]));
+        const int ws = lo2 / nb, b = lo2 - ws * nb;
+        return __ldcg(a.pub_ids + (int64_t)(par * a.w_max + ws) * a.n_total + neuron_base + (int64_t)b * tb_full +
+                      (g - cnt_s[lo2]));
       };
-      // header (32 B) and row start of the block's piece of spike g
-      auto load_hdr = [&](uint32_t g, uint4& h0, uint4& h1, unsigned long long& row) {
-        const uint32_t id = spike_id(g);
+      // header (32 B) and row start of the block's piece of spike g, fetched asynchronously into
+      // the header slot of its round
+      auto fetch_hdr = [&](uint32_t x, uint32_t k) {
+        const uint32_t id = spike_id(x * B + k);
+        unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
         const uint4* hp = a.hdr + 2 * (hdr_net + (int64_t)id * nb + wk.group);
-        h0 = __ldg(hp);
-        h1 = __ldg(hp + 1);
-        row = __ldg(a.row_base + row_off + id);
+        cp_async16(h, hp);
+        cp_async16(h + 16, hp + 1);
+        cp_async8(h + 32, a.row_base + row_off + id);
       };
-      auto hdr_slot = [&](uint32_t x) { return hdr_s + (x % (kStages + 1)) * (2 * kSpikeBatch); };
-      auto rowb_slot = [&](uint32_t x) { return rowb_s + (x % (kStages + 1)) * kSpikeBatch; };
-      // stage the records of round x: warp w copies spikes w, w + n_warps, ... (lanes over 16-byte
-      // chunks) and records where each piece landed
+      // piece descriptor of spike k of round x (64 bytes, one lane writes it):
+      //   [0] 16-byte-aligned global addresses of the weight and meta pieces
+      //   [1] x: weight chunks | meta chunks << 16; y: weight offset | meta offset << 8 | slot << 16
+      //   [2..3] the header's u16 end[w] (bytes 32 + 2w)
+      auto desc_slot = [&](uint32_t x) { return desc_s + (x % (kStages + 1)) * (4 * kSpikeBatch); };
+      auto store_desc = [&](uint32_t x, uint32_t k) {
+        const unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
+        const uint4 h0 = *reinterpret_cast<const uint4*>(h), h1 = *reinterpret_cast<const uint4*>(h + 16);
+        const unsigned long long row = *reinterpret_cast<const unsigned long long*>(h + 32);
+        const uint32_t g = x * B + k;
+        int ws = 0;
+        while (ws + 1 < Wn && woffs[ws + 1] <= g) ++ws;
+        const uint32_t len = h1.w >> 16;
+        const unsigned long long r0 = (unsigned long long)rec_net + row + (h0.x & 0xffffu);
+        const unsigned long long wbyte = r0 * kWsz, mbyte = r0 * 2ull;
+        const uint32_t wal = (uint32_t)(wbyte & 15u), mal = (uint32_t)(mbyte & 15u);
+        const uint32_t nw = len ? (wal + len * kWsz + 15u) >> 4 : 0u;
+        const uint32_t nm = len ? (mal + len * 2u + 15u) >> 4 : 0u;
+        const unsigned long long gw = reinterpret_cast<unsigned long long>(a.rec_w) + (wbyte & ~15ull);
+        const unsigned long long gm = reinterpret_cast<unsigned long long>(a.rec_meta) + (mbyte & ~15ull);
+        uint4* d = desc_slot(x) + 4 * k;
+        d[0] = make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), (uint32_t)gm, (uint32_t)(gm >> 32));
+        d[1] = make_uint4(nw | (nm << 16), wal | (mal << 8) | ((uint32_t)((tm0 + ws) % D) << 16), 0u, 0u);
+        d[2] = make_uint4(h0.y, h0.z, h0.w, h1.x);
+        d[3] = make_uint4(h1.y, h1.z, h1.w, 0u);
+      };
+      // stage the records of round x: warp w copies spikes w, w + n_warps, ...; lane c copies the
+      // 16-byte chunk c of the weight piece followed by the meta piece
       auto issue_round = [&](uint32_t x) {
         if (x >= R) return;
-        const uint4* hs = hdr_slot(x);
-        const unsigned long long* rb = rowb_slot(x);
+        const uint4* ds = desc_slot(x);
         const uint32_t n = min(B, S_tot - x * B);
-        const uint32_t sb = (x % kStages) * (B * cap);
-        SpikeInfo* inf = info + (x % kStages) * kSpikeBatch;
+        unsigned char* sb = stage + (x % kStages) * (B * cap);
         for (uint32_t k = warp; k < n; k += n_warps) {
-          const uint4 h0 = hs[2 * k], h1 = hs[2 * k + 1];
-          const uint32_t len = h1.w >> 16;
-          const uint64_t r0 = (uint64_t)rec_net + rb[k] + (h0.x & 0xffffu);
-          const uint32_t d = sb + k * cap;
-          if (lane == 0) {
-            const uint32_t g = x * B + k;
-            int ws = 0;
-            while (ws + 1 < Wn && woffs[ws + 1] <= g) ++ws;
-            SpikeInfo si;
-            si.woff = d + (uint32_t)((r0 * wsz) & 15u);
-            si.moff = d + cap_w + (uint32_t)((r0 * 2u) & 15u);
-            si.endw[0] = h0.y; si.endw[1] = h0.z; si.endw[2] = h0.w;
-            si.endw[3] = h1.x; si.endw[4] = h1.y; si.endw[5] = h1.z; si.endw[6] = h1.w;
-            si.tm = (uint32_t)((tm0 + ws) % D);
-            inf[k] = si;
+          const uint4 d0 = ds[4 * k];
+          const uint32_t cnt = ds[4 * k + 1].x;
+          const uint32_t nw = cnt & 0xffffu, nt2 = nw + (cnt >> 16);
+          const unsigned char* gw = reinterpret_cast<const unsigned char*>(((unsigned long long)d0.y << 32) | d0.x);
+          const unsigned char* gm = reinterpret_cast<const unsigned char*>(((unsigned long long)d0.w << 32) | d0.z);
+          unsigned char* dst = sb + k * cap;
+          for (uint32_t c = lane; c < nt2; c += 32) {
+            const bool isw = c < nw;
+            const uint32_t o = 16u * (isw ? c : c - nw);
+            cp_async16(dst + (isw ? 0u : cap_w) + o, (isw ? gw : gm) + o);
           }
-          if (len == 0) continue;
-          const uint64_t wb0 = (r0 * wsz) & ~15ull, wb1 = ((r0 + len) * wsz + 15) & ~15ull;
-          const uint64_t mb0 = (r0 * 2u) & ~15ull, mb1 = ((r0 + len) * 2u + 15) & ~15ull;
-          const unsigned char* gw = reinterpret_cast<const unsigned char*>(a.rec_w) + wb0;
-          const unsigned char* gm = reinterpret_cast<const unsigned char*>(a.rec_meta) + mb0;
-          const uint32_t nw = (uint32_t)((wb1 - wb0) >> 4), nm = (uint32_t)((mb1 - mb0) >> 4);
-          for (uint32_t c = lane; c < nw; c += 32) cp_async16(stage + d + 16u * c, gw + 16u * c);
-          for (uint32_t c = lane; c < nm; c += 32) cp_async16(stage + d + cap_w + 16u * c, gm + 16u * c);
         }
       };
 
+      // Pipeline (iteration r): issue the records of round r + kStages - 1 and the headers of round
+      // r + kHdrAhead; wait until round r's copy group is complete; build the descriptors of round
+      // r + kStages from headers fetched kHdrAhead - kStages iterations earlier (whose groups are
+      // complete by then since kHdrAhead >= 2 kStages - 1); fold round r.
       if (R > 0) {
-        // headers of the first kStages rounds, then the records of the first kStages - 1 rounds
+        // headers of the first kStages rounds (waited for here), descriptors, then the headers of
+        // rounds kStages .. kHdrAhead - 1 and the records of the first kStages - 1 rounds
         for (uint32_t i = tid; i < min(R, (uint32_t)kStages) * B; i += blockDim.x) {
           const uint32_t x = i / B, k = i % B;
-          if (x * B + k < S_tot) {
-            uint4 h0, h1;
-            unsigned long long row;
-            load_hdr(x * B + k, h0, h1, row);
-            hdr_slot(x)[2 * k] = h0;
-            hdr_slot(x)[2 * k + 1] = h1;
-            rowb_slot(x)[k] = row;
-          }
+          if (x * B + k < S_tot) fetch_hdr(x, k);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        for (uint32_t i = tid; i < min(R, (uint32_t)kStages) * B; i += blockDim.x) {
+          const uint32_t x = i / B, k = i % B;
+          if (x * B + k < S_tot) store_desc(x, k);
         }
         __syncthreads();
+        for (uint32_t i = tid; i < (uint32_t)(kHdrAhead - kStages) * B; i += blockDim.x) {
+          const uint32_t x = kStages + i / B, k = i % B;
+          if (x < R && x * B + k < S_tot) fetch_hdr(x, k);
+        }
         for (int x = 0; x < kStages - 1; ++x) {
           issue_round((uint32_t)x);
           cp_async_commit();
@@ -491,42 +639,53 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
       }
       const uint32_t wbase_t = (uint32_t)(warp * tw);
       uint8_t* wtags = kRingSmem ? tags : tags + (size_t)warp * kTagHash;
+      const uint32_t lanes_lt = lanemask_lt();
       for (uint32_t r = 0; r < R; ++r) {
         issue_round(r + kStages - 1);
+        {
+          const uint32_t xh = r + kHdrAhead;
+          if (tid < (int)B && xh < R && xh * B + tid < S_tot) fetch_hdr(xh, (uint32_t)tid);
+        }
         cp_async_commit();
-        // header of round r + kStages into registers (stored after the fold)
-        uint4 nh0 = make_uint4(0, 0, 0, 0), nh1 = nh0;
-        unsigned long long nrow = 0;
-        const uint32_t xn = r + kStages;
-        const bool have_next = tid < (int)B && xn < R && xn * B + tid < S_tot;
-        if (have_next) load_hdr(xn * B + tid, nh0, nh1, nrow);
         cp_async_wait<kStages - 1>();
         __syncthreads();
+        {
+          const uint32_t xn = r + kStages;
+          if (tid < (int)B && xn < R && xn * B + tid < S_tot) store_desc(xn, (uint32_t)tid);
+        }
 
         // ---- fold round r: each warp, its target sub-range of every staged piece, in spike order
         {
-          const SpikeInfo* inf = info + (r % kStages) * kSpikeBatch;
+          const unsigned char* ds = reinterpret_cast<const unsigned char*>(desc_slot(r));
           const uint32_t n = min(B, S_tot - r * B);
-          uint32_t len_k = 0, wb_k = 0, mb_k = 0, tm_k = 0;
+          const uint32_t sbase = (r % kStages) * (B * cap);
+          uint32_t len_k = 0, wb_k = 0, mb_k = 0, sb_k = 0;
           if ((uint32_t)lane < n) {
-            const uint16_t* ends = reinterpret_cast<const uint16_t*>(inf[lane].endw);
-            const uint32_t e0 = warp ? ends[warp - 1] : 0u, e1 = ends[warp];
+            const unsigned char* dk = ds + 64u * lane;
+            const uint32_t e1 = *reinterpret_cast<const uint16_t*>(dk + 32 + 2 * warp);
+            const uint32_t e0 = warp ? *reinterpret_cast<const uint16_t*>(dk + 30 + 2 * warp) : 0u;
+            const uint32_t aux = *reinterpret_cast<const uint32_t*>(dk + 20);
             len_k = e1 - e0;
-            wb_k = inf[lane].woff + e0 * wsz;
-            mb_k = inf[lane].moff + e0 * 2u;
-            tm_k = inf[lane].tm;
+            const uint32_t pk = sbase + (uint32_t)lane * cap;
+            wb_k = pk + (aux & 15u) + e0 * kWsz;
+            mb_k = pk + cap_w + ((aux >> 8) & 15u) + e0 * 2u;
+            sb_k = (aux >> 16) + (uint32_t)d_min;
           }
-          // compact the non-empty pieces (their order is the spike order)
+          // pieces in spike order; empty ones are dropped so that segment starts are distinct
           const uint32_t ne = __ballot_sync(0xffffffffu, len_k > 0);
           const int n_ne = __popc(ne);
-          if (len_k > 0) perm[__popc(ne & lanemask_lt())] = (uint8_t)lane;
-          __syncwarp();
-          const int src_lane = (lane < n_ne) ? (int)perm[lane] : 0;
-          const uint32_t c_wb = __shfl_sync(0xffffffffu, wb_k, src_lane);
-          const uint32_t c_mb = __shfl_sync(0xffffffffu, mb_k, src_lane);
-          const uint32_t c_tm = __shfl_sync(0xffffffffu, tm_k, src_lane);
-          uint32_t c_len = __shfl_sync(0xffffffffu, len_k, src_lane);
-          if (lane >= n_ne) c_len = 0;
+          uint32_t c_len = len_k, c_wb = wb_k, c_mb = mb_k, c_sb = sb_k;
+          if (ne != (0xffffffffu >> (32 - max(n_ne, 1))) || n_ne == 0) {
+            if (len_k > 0) perm[__popc(ne & lanes_lt)] = (uint8_t)lane;
+            __syncwarp();
+            const int src_lane = (lane < n_ne) ? (int)perm[lane] : 0;
+            c_len = __shfl_sync(0xffffffffu, len_k, src_lane);
+            c_wb = __shfl_sync(0xffffffffu, wb_k, src_lane);
+            c_mb = __shfl_sync(0xffffffffu, mb_k, src_lane);
+            c_sb = __shfl_sync(0xffffffffu, sb_k, src_lane);
+            if (lane >= n_ne) c_len = 0;
+            __syncwarp();
+          }
           uint32_t c_end = c_len;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
@@ -536,28 +695,28 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
           const uint32_t c_start = c_end - c_len;
           const uint32_t total = __shfl_sync(0xffffffffu, c_end, 31);
           if (lane == 0) my_events += total;
+          // per segment: staging addresses of entry q are base + q * size (q counts over the round)
+          const uint32_t c_wadj = c_wb - c_start * kWsz, c_madj = c_mb - c_start * 2u;
           int cur = -1;
           // key and weight of the lane's entry in the chunk starting at cb (0xffffffff: none)
           auto chunk_key = [&](uint32_t cb, float& wv) -> uint32_t {
-            const uint32_t bits = (lane < n_ne && c_start >= cb && c_start < cb + 32) ? (1u << (c_start - cb)) : 0u;
+            const uint32_t bits = (lane < n_ne && c_start - cb < 32u) ? (1u << (c_start - cb)) : 0u;
             const uint32_t sm = __reduce_or_sync(0xffffffffu, bits);
-            const int seg = cur + __popc(sm & (0xffffffffu >> (31 - lane)));
+            const int seg = cur + __popc(sm & (lanes_lt | (1u << lane)));
             cur += __popc(sm);
-            const uint32_t q = cb + lane;
             const int sl = seg & 31;
-            const uint32_t swb = __shfl_sync(0xffffffffu, c_wb, sl);
-            const uint32_t smb = __shfl_sync(0xffffffffu, c_mb, sl);
-            const uint32_t scs = __shfl_sync(0xffffffffu, c_start, sl);
-            const uint32_t stm = __shfl_sync(0xffffffffu, c_tm, sl);
+            const uint32_t wa = __shfl_sync(0xffffffffu, c_wadj, sl);
+            const uint32_t ma = __shfl_sync(0xffffffffu, c_madj, sl);
+            const uint32_t sbv = __shfl_sync(0xffffffffu, c_sb, sl);
+            const uint32_t q = cb + lane;
             wv = 0.0f;
             if (q >= total) return 0xffffffffu;
-            const uint32_t m = q - scs;
-            const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + smb + 2u * m);
-            wv = bf16 ? __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + swb + 2u * m))
-                      : *reinterpret_cast<const float*>(stage + swb + 4u * m);
-            int slot = (int)stm + d_min + (int)(meta & dmask);
-            if (slot >= D) slot -= D;
-            return (uint32_t)slot * (uint32_t)nt + wbase_t + (meta >> dbits);
+            const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + ma + 2u * q);
+            if constexpr (kBf16) wv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + wa + 2u * q));
+            else wv = *reinterpret_cast<const float*>(stage + wa + 4u * q);
+            uint32_t slot = sbv + (meta & dmask);
+            if (slot >= (uint32_t)D) slot -= (uint32_t)D;
+            return slot * (uint32_t)nt + wbase_t + (meta >> dbits);
           };
           uint32_t e = 0;
           for (; e + 3 * 32 < total; e += 4 * 32) {  // four chunks at a time while they are all used
@@ -574,11 +733,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
             fold_chunk<kRingSmem>(ring, wtags, key, wv, lane);
           }
         }
-        if (have_next) {
-          hdr_slot(xn)[2 * tid] = nh0;
-          hdr_slot(xn)[2 * tid + 1] = nh1;
-          rowb_slot(xn)[tid] = nrow;
-        }
         __syncthreads();
       }
       cp_async_wait<0>();
@@ -594,9 +748,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
     for (int j = tid; j < nt; j += blockDim.x) {
       const float in = rs[j];
       rs[j] = 0.0f;
-      const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)tl, kStreamPoisson, 0u), seed_lo, seed_hi);
       float cur = sI[j];
-      i_half(cur, in, rr.x, nd, thr);
+      i_half_k(cur, in, pk[j], nd);  // filled at the last barrier for step tl
       sI[j] = cur;
     }
     __syncthreads();
@@ -615,6 +768,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_step(const StepArgs a) {
   if (persistent && do_deliver && wk.group == 0 && tid == 0 && a.raster_step != nullptr)
     a.raster_count[wk.net] = raster_total;
   if (persistent && blk == 0 && tid == 0 && a.t_fixed < 0 && !aborted) *a.step_counter = t_start + a.n_steps;
+  if (persistent && tid == 0 && !aborted) a.pub_flag[blk] = epoch;  // windows completed, for the next launch
 }
 
 // split mode: advance the step counter and the per-network spike totals after a window
@@ -631,7 +785,8 @@ __global__ void k_advance(const StepArgs a, int n_nets, int wn) {
 }
 
 cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s) {
-  void (*kern)(StepArgs) = a.ring_smem ? k_step<true> : k_step<false>;
+  void (*kern)(StepArgs) = a.ring_smem ? (a.bf16 ? k_step<true, true> : k_step<true, false>)
+                                       : (a.bf16 ? k_step<false, true> : k_step<false, false>);
   if (cooperative) {
     // all blocks must be co-resident: they wait on each other at the window barrier
     cudaLaunchConfig_t cfg = {};
@@ -666,15 +821,18 @@ void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m) {
 }
 
 cudaError_t step_kernel_attributes(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*kerns[4])(StepArgs) = {k_step<true, false>, k_step<true, true>, k_step<false, false>, k_step<false, true>};
+  for (auto k : kerns) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int step_occupancy(int threads, size_t smem, bool ring_smem) {
   int n = 0;
-  cudaError_t e = ring_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<true>, threads, smem)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false>, threads, smem);
+  cudaError_t e = ring_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<true, false>, threads, smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, false>, threads, smem);
   return e == cudaSuccess ? n : 0;
 }
 
