@@ -1,7 +1,7 @@
 """Benchmark: synaptic events/s and real-time factor of the spike-delivery hot path on one GB300.
 
-One benchmark step = one cortex_simulate call of --sim-steps simulation steps (default 1000 steps =
-100 ms of simulated time) of the balanced random network N = 112,500, K = 11,250, FP32 weights
+One benchmark step = one cortex_simulate call of --sim-steps simulation steps (default 10,000 steps
+= 1 s of simulated time) of the balanced random network N = 112,500, K = 11,250, FP32 weights
 (1.27e9 synapses, about 9.4 GB on the device, so every step reads far more than the 129 MB L2).
 Each simulation step runs the whole hot path: neuron update, spike compaction, publication, grid
 barrier and delivery.  Inputs are synthetic (a seeded network), built on the device before timing.
@@ -9,7 +9,9 @@ barrier and delivery.  Inputs are synthetic (a seeded network), built on the dev
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Under torchrun every rank simulates its own replica (weak scaling, no collective on the data
-path); rank 0 prints one JSON line.  --impl reference times the CPU oracle on the host cores
+path); rank 0 prints one JSON line.  At one GPU the line also carries "forms": the same metric for
+the BF16-weight network (N = 1e6, K = 11,250) and for the batch of 64 networks, each timed after
+the main measurement on the same GPU.  --impl reference times the CPU oracle on the host cores
 (bounded sample of the same network) and prints the same metric.
 """
 from __future__ import annotations
@@ -75,7 +77,8 @@ def start_oracle(cfg_name, sample_steps, n_samples):
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 20 ms; stop() keeps those taken inside [mark_start, mark_end]."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -83,36 +86,63 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.path = os.path.join("/tmp", f"cortex_clocks_{os.getpid()}.csv")
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 3 s) for the first sample so that sampling covers the timed region
+        t_end = time.time() + 3.0
+        while time.time() < t_end:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
-        if not rows:
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, parts[1:]))
+        inside = [r for ts, r in rows if ts is not None and self.t0 is not None and self.t1 is not None
+                  and self.t0 - 0.02 <= ts <= self.t1 + 0.02]
+        use = inside if inside else [r for _, r in rows]
+        if not use:
             return None
-        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
-        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        sm = sorted(float(r[1]) for r in use if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in use if r[2].replace(".", "").isdigit()), default=None)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in use for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(use), "samples_in_timed_region": len(inside)}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -176,27 +206,31 @@ def our_arm(args):
 
     for _ in range(args.warmup):
         net.simulate(args.sim_steps)
-    net.clear_spikes()
+        net.clear_spikes()
     barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     ev_a = torch.cuda.Event(enable_timing=True)
     ev_b = torch.cuda.Event(enable_timing=True)
-    e_before = net.stats()["events"]
+    st_b = net.stats()
+    e_before, s_before = st_b["events"], st_b["spikes"]
+    clocks.mark_start()
     ev_a.record(stream)
     kern_ms = 0.0
     for _ in range(args.steps):
         net.simulate(args.sim_steps)          # launches on `stream`
         kern_ms += net.stats()["simulate_ms"]
+        net.clear_spikes()                    # the device raster keeps one step's spikes
     ev_b.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier()
     clk = clocks.stop()
     ms = ev_a.elapsed_time(ev_b)
     st = net.stats()
     events = st["events"] - e_before
-    spikes = st["spikes"]
+    spikes = st["spikes"] - s_before
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     e = torch.tensor([float(events)], dtype=torch.float64, device="cuda")
     if dist is not None:
@@ -266,12 +300,50 @@ def our_arm(args):
         p.join(timeout=5)
         if p.is_alive():
             p.terminate()
+    net.close()
+    if world == 1 and not args.no_forms:
+        line["forms"] = {"bf16": _form(cortex, W, "c3", args, stream, peak, peak_kind),
+                         "batched": _form(cortex, W, "c4", args, stream, peak, peak_kind)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    net.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _form(cortex, W, name, args, stream, peak, peak_kind):
+    """events/s, RTF and kernel roofline of another configuration on the same GPU: the BF16-weight
+    network (c3) or the 64-network batch (c4).  One untimed launch, then --form-steps steps."""
+    cfg = W.CONFIGS[name]
+    if name == "c4":
+        specs, seeds = W.batch_specs()
+        net = cortex.Network(specs, seeds, cortex.make_options(steps_per_launch=args.steps_per_launch), stream=stream)
+        bpe = BYTES_PER_EVENT[0]
+    else:
+        net = cortex.Network(cfg["spec"], cfg["seed"], cortex.make_options(steps_per_launch=args.steps_per_launch),
+                             stream=stream)
+        bpe = BYTES_PER_EVENT[cfg["spec"].weight_dtype]
+    st0 = net.stats()
+    net.simulate(args.steps_per_launch)
+    e0 = net.stats()["events"]
+    t0 = time.perf_counter()
+    net.simulate(args.form_steps)
+    wall = time.perf_counter() - t0
+    st = net.stats()
+    ev = st["events"] - e0
+    ms = st["simulate_ms"]
+    launches = max(1, -(-args.form_steps // args.steps_per_launch))
+    achieved = ev * bpe / (ms * 1e-3) / 1e9
+    sim_s = args.form_steps * 0.1e-3
+    out = {"workload": cfg["name"], "value": ev / (ms * 1e-3), "unit": UNIT, "rtf": (ms * 1e-3) / sim_s,
+           "sim_steps": args.form_steps, "wall_value": ev / wall, "n_nets": st0["n_nets"],
+           "neurons": st0["n_neurons"], "synapses": st0["n_synapses"], "build_ms": st0["build_ms"],
+           "dtype": "bf16" if bpe == 5 else "f32",
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (persistent)",
+                        "launch_ms": ms / launches}}
+    net.close()
+    return out
 
 
 def _traffic(events_per_launch, spec):
@@ -341,7 +413,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c1")
-    ap.add_argument("--sim-steps", type=int, default=1000)
+    ap.add_argument("--sim-steps", type=int, default=10000)
     ap.add_argument("--steps-per-launch", type=int, default=1000)
     ap.add_argument("--cpu-sample-steps", type=int, default=1500)
     ap.add_argument("--cpu-timeout", type=float, default=900.0)
@@ -350,6 +422,8 @@ def main():
     ap.add_argument("--mode", default="simulate", choices=["simulate", "deliver"])
     ap.add_argument("--spikes", type=int, default=10000)
     ap.add_argument("--warps", type=int, default=0, help="warps per block (0: library default)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched forms")
+    ap.add_argument("--form-steps", type=int, default=2000, help="simulation steps timed per form")
     args = ap.parse_args()
     if args.mode == "deliver":
         return deliver_arm(args)

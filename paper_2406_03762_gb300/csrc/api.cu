@@ -74,6 +74,7 @@ struct cortex_net {
   int n_warps = 14, threads = 448, n_blocks = 0, n_sm = 0;
   int w_max = 1, w_split = 1, max_nt = 0, max_depth = 0, max_nb = 0;
   bool ring_smem = false;
+  bool ring_red = false;  // global ring adds by the L2 reduction unit (exact for the weights)
   int mode = CORTEX_MODE_PERSISTENT;
   int stage_bytes = 0, batch = 32, cap_w = 0, cap_m = 0;
   size_t smem = 0;
@@ -209,6 +210,7 @@ StepArgs make_args(cortex_net* h) {
   a.max_depth = h->max_depth;
   a.max_nb = h->max_nb;
   a.timeout_ns = h->timeout_ns;
+  a.ring_red = h->ring_red ? 1 : 0;
   a.bf16 = h->wdtype == CORTEX_BF16 ? 1 : 0;
   a.withhold_block = h->withhold_block;
   a.t_fixed = -1;
@@ -341,6 +343,15 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
                                             " B, state " + std::to_string(base) + " B, staging per spike " +
                                             std::to_string(per_spike) + " B)");
   h->ring_smem = smem_ring;
+  {
+    // reductions flush subnormals: allowed when every weight is 0 or >= 2^-102 in magnitude (with
+    // margin for bf16 rounding), so that no partial sum of a cell can be subnormal
+    bool ok = true;
+    for (const auto& p : h->params)
+      for (float w : {p.j_exc, p.j_inh})
+        ok = ok && (w == 0.0f || std::fabs(w) >= std::ldexp(1.0f, -102));
+    h->ring_red = ok && !smem_ring;
+  }
   h->batch = b;
   h->stage_bytes = (int)(per_spike * b);
   h->smem = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, smem_ring, h->stage_bytes);

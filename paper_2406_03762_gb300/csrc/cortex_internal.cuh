@@ -107,6 +107,7 @@ struct StepArgs {
   int32_t phases;                     // kPhaseUpdate | kPhaseDeliver
   int32_t ring_smem;                  // 1: ring slice in shared memory
   int32_t bf16;                       // 1: weights stored as bf16 (all networks of a handle)
+  int32_t ring_red;                   // 1: adds into a global ring use the L2 reduction unit
   int32_t stage_bytes;                // shared staging capacity for record segments
   int32_t batch;                      // spikes per delivery round
   int32_t cap_w, cap_m;               // staging bytes per spike: weight stream, meta stream

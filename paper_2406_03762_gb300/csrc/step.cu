@@ -136,12 +136,35 @@ __device__ __forceinline__ void i_half(float& cur, float in, uint32_t u, const N
   i_half_k(cur, in, poisson_k(u, nd, thr), nd);
 }
 
+// One ring cell += w.  A ring in shared memory: load, add, store.  A ring in global memory: the
+// same, or (red) an add performed by the L2 reduction unit, which rounds to nearest even like the
+// load-add-store but flushes subnormal operands and results to zero.  The host selects red only
+// when every weight is zero or at least 2^-103 in magnitude: every partial sum of a cell is then an
+// integer multiple of the smallest weight's ulp (>= 2^-126), so no operand or result is subnormal
+// and both forms give the same bits.  Lanes that add to one cell are ordered by __syncwarp, which
+// orders their memory operations.
+template <bool kRingSmem>
+__device__ __forceinline__ void ring_add(float* ring, uint32_t key, float w, bool red) {
+  if (!kRingSmem && red) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(ring + key), "f"(w) : "memory");
+  } else {
+    ring[key] = __fadd_rn(ring[key], w);
+  }
+}
+
+// a ring cell read by the update: a global ring bypasses L1 (reductions are performed in L2)
+template <bool kRingSmem>
+__device__ __forceinline__ float ring_read(const float* p) {
+  if (kRingSmem) return *p;
+  return __ldcg(p);
+}
+
 // Add the weights of one 32-lane chunk to their ring cells (key = cell, 0xffffffff = no entry).
 // Lanes hold entries in stream order.  Lanes whose cell no other lane of the chunk touches add at
 // once; lanes that share a cell add one by one in lane order, so every cell folds its weights in
 // stream order.  Sharing is found by writing the lane id into a tag per cell and reading it back.
 template <bool kRingSmem>
-__device__ __forceinline__ void fold_chunk(float* ring, uint8_t* wtags, uint32_t key, float w, int lane) {
+__device__ __forceinline__ void fold_chunk(float* ring, uint8_t* wtags, uint32_t key, float w, int lane, bool red) {
   const bool valid = key != 0xffffffffu;
   // shared ring: one tag per cell (warps own disjoint cells); global ring: the warp's hashed table
   uint8_t* tg = kRingSmem ? wtags + (valid ? key : 0u) : wtags + (key & (uint32_t)(kTagHash - 1));
@@ -151,16 +174,16 @@ __device__ __forceinline__ void fold_chunk(float* ring, uint8_t* wtags, uint32_t
   const bool loser = valid && t != (uint32_t)lane;
   const uint32_t losers = __ballot_sync(0xffffffffu, loser);
   if (losers == 0) {
-    if (valid) ring[key] = __fadd_rn(ring[key], w);
+    if (valid) ring_add<kRingSmem>(ring, key, w, red);
   } else {
     const uint32_t winners = __reduce_or_sync(0xffffffffu, loser ? (1u << t) : 0u);
     const uint32_t dup = losers | winners;
-    if (valid && !((dup >> lane) & 1u)) ring[key] = __fadd_rn(ring[key], w);
+    if (valid && !((dup >> lane) & 1u)) ring_add<kRingSmem>(ring, key, w, red);
     __syncwarp();
     uint32_t m = dup;
     while (m) {
       const int first = __ffs(m) - 1;
-      if (lane == first) ring[key] = __fadd_rn(ring[key], w);
+      if (lane == first) ring_add<kRingSmem>(ring, key, w, red);
       __syncwarp();
       m &= m - 1u;
     }
@@ -200,6 +223,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   const int nt = wk.nt, tw = wk.tw;
   const int tb_full = a.work[first_block].nt;  // targets of the network's full blocks
   const bool persistent = (a.phases & kPhaseBarrier) != 0;
+  const bool ring_red = a.ring_red != 0;
   const bool do_update = (a.phases & kPhaseUpdate) != 0;
   const bool do_deliver = (a.phases & kPhaseDeliver) != 0;
   const uint32_t B = (uint32_t)a.batch, cap_w = (uint32_t)a.cap_w, cap = (uint32_t)(a.cap_w + a.cap_m);
@@ -295,13 +319,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
             int32_t r = sR[j];
             if (defer) {
               if (prev) {
-                const float in = rs[j];
+                const float in = ring_read<kRingSmem>(rs + j);
                 rs[j] = 0.0f;
                 i_half_k(cur, in, pk[ws * nt + j], nd);
               }
               spk = v_half(v, cur, r, nd);
             } else {
-              const float in = rs[j];
+              const float in = ring_read<kRingSmem>(rs + j);
               rs[j] = 0.0f;
               const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
               spk = v_half(v, cur, r, nd);
@@ -725,12 +749,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) fold_chunk<kRingSmem>(ring, wtags, key[u], wv[u], lane);
+            for (int u = 0; u < 4; ++u) fold_chunk<kRingSmem>(ring, wtags, key[u], wv[u], lane, ring_red);
           }
           for (; e < total; e += 32) {
             float wv;
             const uint32_t key = chunk_key(e, wv);
-            fold_chunk<kRingSmem>(ring, wtags, key, wv, lane);
+            fold_chunk<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
           }
         }
         __syncthreads();
@@ -746,7 +770,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
     const long long tl = t_start + a.n_steps - 1;
     float* rs = ring + (int64_t)(tl % D) * nt;
     for (int j = tid; j < nt; j += blockDim.x) {
-      const float in = rs[j];
+      const float in = ring_read<kRingSmem>(rs + j);
       rs[j] = 0.0f;
       float cur = sI[j];
       i_half_k(cur, in, pk[j], nd);  // filled at the last barrier for step tl
