@@ -315,9 +315,14 @@ def _form(cortex, W, name, args, stream, peak, peak_kind):
     """events/s, RTF and kernel roofline of another configuration on the same GPU: the BF16-weight
     network (c3) or the 64-network batch (c4).  One untimed launch, then --form-steps steps."""
     cfg = W.CONFIGS[name]
+    plan = None
     if name == "c4":
         specs, seeds = W.batch_specs()
-        net = cortex.Network(specs, seeds, cortex.make_options(steps_per_launch=args.steps_per_launch), stream=stream)
+        base = cortex.make_options(steps_per_launch=args.steps_per_launch)
+        best, tune_ms, n_tried = cortex.autotune(specs, seeds, base, trial_steps=args.steps_per_launch, stream=stream)
+        plan = {"autotuned": True, "warps_per_block": best.warps_per_block, "balance": best.balance,
+                "candidates": n_tried, "trial_ms_per_step": tune_ms}
+        net = cortex.Network(specs, seeds, best, stream=stream)
         bpe = BYTES_PER_EVENT[0]
     else:
         net = cortex.Network(cfg["spec"], cfg["seed"], cortex.make_options(steps_per_launch=args.steps_per_launch),
@@ -342,6 +347,8 @@ def _form(cortex, W, name, args, stream, peak, peak_kind):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (persistent)",
                         "launch_ms": ms / launches}}
+    if plan is not None:
+        out["plan"] = plan
     net.close()
     return out
 

@@ -78,6 +78,8 @@ typedef struct cortex_options {
   int32_t use_graph;                 /* 0 = auto (on), 1 = on, -1 = off */
   int64_t raster_capacity;           /* 0 = auto; spikes kept on the device per network */
   double barrier_timeout_ms;         /* 0 = 2000 ms; device waits give up after this */
+  int32_t balance;                   /* block plan of a batch: 0 = equal targets per block,
+                                        1 = equal synapses per block (targets x in-degree) */
   int32_t test_withhold_block;       /* test hook, 0 = off.  b + 1: block b of the persistent
                                         kernel never publishes its spikes, so every block's bounded
                                         wait at the window barrier runs out and cortex_simulate
@@ -120,6 +122,20 @@ int cortex_build(const cortex_params* params, uint64_t seed, const cortex_option
  * errors as cortex_build. */
 int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32_t n_nets,
                        const cortex_options* opts, void* stream, cortex_net** out);
+
+/* Autotuner (the paper has no counterpart: its partition is fixed by processes and threads).
+ * Builds the network(s) of params / seeds with each candidate plan -- warps per block, i.e. the
+ * number and width of the per-warp indegree sub-graphs (Sec. III-B), in {8, 10, 12, 14}, times the
+ * block plan (base->balance 0 or 1) -- simulates trial_steps > 0 steps after one untimed launch,
+ * frees it, and returns in *best the options of the fastest candidate (the other fields copied
+ * from base, which may be NULL).  The simulation results do not depend on the plan (the
+ * summation order is fixed by emission step, source and draw); only the time does.
+ * best_ms_per_step and n_tried (candidates that could be built) may be NULL.  Candidates that
+ * exceed the layout limits are skipped.  Errors: CORTEX_ERR_ARG, CORTEX_ERR_UNSUPPORTED (no
+ * candidate could be built), CORTEX_ERR_CUDA, CORTEX_ERR_TIMEOUT, CORTEX_ERR_OOM. */
+int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t n_nets,
+                    const cortex_options* base, int32_t trial_steps, void* stream,
+                    cortex_options* best, double* best_ms_per_step, int32_t* n_tried);
 
 /* Advance every network by n_steps >= 0 steps from the current step (Sec. II-B loop: deliver,
  * update, compact spikes).  Continuing in pieces gives the same result as one call.

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
         ("ring", ctypes.c_int32), ("mode", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
         ("targets_per_block", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("raster_capacity", ctypes.c_int64), ("barrier_timeout_ms", ctypes.c_double),
-        ("test_withhold_block", ctypes.c_int32),
+        ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
     ]
 
 
@@ -63,6 +63,7 @@ EXPORTED = [
     "cortex_build", "cortex_build_batch", "cortex_simulate", "cortex_spikes", "cortex_clear_spikes",
     "cortex_stats", "cortex_export_synapses", "cortex_get_state", "cortex_constants", "cortex_deliver",
     "cortex_philox", "cortex_free", "cortex_strerror", "cortex_last_error", "cortex_subgraph_noalloc",
+    "cortex_autotune",
 ]
 
 _lib = None
@@ -101,6 +102,8 @@ def load(build_if_missing: bool = False):
                                  ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_int64)]
     L.cortex_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int64, P(ctypes.c_uint32)]
     L.cortex_subgraph_noalloc.argtypes = [P(Params), ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp]
+    L.cortex_autotune.argtypes = [P(Params), P(ctypes.c_uint64), ctypes.c_int32, P(Options), ctypes.c_int32, vp,
+                                  P(Options), P(ctypes.c_double), P(ctypes.c_int32)]
     for name in EXPORTED:
         if name not in ("cortex_free", "cortex_strerror", "cortex_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -145,6 +148,23 @@ def _stream_handle(stream) -> int | None:
     if isinstance(stream, int):
         return stream
     return int(getattr(stream, "cuda_stream"))
+
+
+def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000, stream=None):
+    """cortex_autotune: the fastest plan (warps per block x block balance) for these networks.
+    Returns (Options, ms per simulation step, number of candidates built)."""
+    L = load()
+    if not isinstance(specs, (list, tuple)):
+        specs, seeds = [specs], [seeds]
+    arr = (Params * len(specs))(*[params_from_spec(s) for s in specs])
+    sd = (ctypes.c_uint64 * len(specs))(*[int(x) for x in seeds])
+    best = Options()
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int32(0)
+    rc = L.cortex_autotune(arr, sd, len(specs), ctypes.byref(base) if base is not None else None, int(trial_steps),
+                           _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms), ctypes.byref(n))
+    _check(rc, "cortex_autotune")
+    return best, float(ms.value), int(n.value)
 
 
 class Network:

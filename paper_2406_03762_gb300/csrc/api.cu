@@ -133,24 +133,36 @@ int validate_params(const cortex_params& p, std::string& why) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Targets per block for every network so that all blocks are co-resident (one per SM).
+// Targets per block for every network so that all blocks are co-resident (one per SM).  Every
+// network is cut into equal blocks.  balance 0: one target budget T for all networks; balance 1:
+// one synapse budget for all networks (a network of in-degree K gets blocks of about budget / K
+// targets), so that blocks of a batch with uneven in-degrees carry similar delivery work.  The
+// budget grows until the blocks fit on the SMs.
 int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb) {
   const int cap = h->n_sm;  // one block per SM
   const int64_t tmin = 32ll * h->n_warps;
-  int64_t n_total = 0;
-  for (auto& p : h->params) n_total += (int64_t)p.n_exc + p.n_inh;
+  int64_t n_total = 0, syn_total = 0, kmax = 1;
+  for (auto& p : h->params) {
+    const int64_t n = (int64_t)p.n_exc + p.n_inh, k = std::max<int64_t>(1, (int64_t)p.k_exc + p.k_inh);
+    n_total += n;
+    syn_total += n * k;
+    kmax = std::max(kmax, k);
+  }
+  const bool by_syn = o.balance == 1 && o.targets_per_block <= 0;
   int64_t T = std::max<int64_t>(tmin, ceil_div(n_total, cap));
+  int64_t S = std::max<int64_t>(tmin * kmax, ceil_div(syn_total, cap));  // synapse budget (balance 1)
   if (o.targets_per_block > 0) T = std::min<int64_t>(T, o.targets_per_block);
   for (int iter = 0; iter < 10000; ++iter) {
     int64_t blocks = 0;
     tb.assign(h->n_nets, 0);
     for (int b = 0; b < h->n_nets; ++b) {
       const int64_t n = (int64_t)h->params[b].n_exc + h->params[b].n_inh;
-      int64_t t = std::min<int64_t>(n, T);
+      const int64_t k = std::max<int64_t>(1, (int64_t)h->params[b].k_exc + h->params[b].k_inh);
+      int64_t t = by_syn ? std::min<int64_t>(n, std::max<int64_t>(tmin, S / k)) : std::min<int64_t>(n, T);
       // balance the blocks of one network
       const int64_t nb = ceil_div(n, t);
       t = ceil_div(n, nb);
-      tb[b] = (int32_t)t;
+      tb[b] = (int32_t)std::min<int64_t>(t, 1 << 30);
       blocks += nb;
     }
     bool ok = true;
@@ -158,6 +170,7 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
     if (!ok) return fail(CORTEX_ERR_UNSUPPORTED, "targets per block above 65535 (network too large for one GPU plan)");
     if (blocks <= cap || o.targets_per_block > 0) return CORTEX_OK;
     T = T + std::max<int64_t>(1, T / 16);
+    S = S + std::max<int64_t>(1, S / 16);
   }
   return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
 }
@@ -402,6 +415,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..14");
   if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
   if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
+  if (o.balance < 0 || o.balance > 1) return fail(CORTEX_ERR_ARG, "balance");
 
   cortex_net* h = new (std::nothrow) cortex_net();
   if (!h) return fail(CORTEX_ERR_OOM, "handle");
@@ -602,6 +616,48 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
 int cortex_build(const cortex_params* params, uint64_t seed, const cortex_options* opts, void* stream,
                  cortex_net** out) {
   return cortex_build_batch(params, &seed, 1, opts, stream, out);
+}
+
+int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t n_nets, const cortex_options* base,
+                    int32_t trial_steps, void* stream, cortex_options* best, double* best_ms_per_step,
+                    int32_t* n_tried) {
+  if (!params || !seeds || n_nets <= 0 || trial_steps <= 0 || !best) return fail(CORTEX_ERR_ARG, "cortex_autotune: arguments");
+  cortex_options b0;
+  memset(&b0, 0, sizeof(b0));
+  if (base) b0 = *base;
+  // candidates: warps per block (the width of the per-warp sub-graphs) x block plan
+  const int warps[] = {8, 10, 12, 14};
+  double best_ms = -1.0;
+  int tried = 0, last_rc = CORTEX_ERR_UNSUPPORTED;
+  for (int bal = 0; bal <= 1; ++bal)
+    for (int w : warps) {
+      cortex_options o = b0;
+      o.warps_per_block = w;
+      o.balance = bal;
+      cortex_net* h = nullptr;
+      int rc = cortex_build_batch(params, seeds, n_nets, &o, stream, &h);
+      if (rc == CORTEX_OK) rc = cortex_simulate(h, std::min<int64_t>(trial_steps, h->steps_per_launch));  // warm-up
+      double ms = 0.0;
+      if (rc == CORTEX_OK) {
+        rc = cortex_simulate(h, trial_steps);
+        ms = h->sim_ms;
+      }
+      if (h) cortex_free(h);
+      if (rc == CORTEX_ERR_CUDA || rc == CORTEX_ERR_TIMEOUT) return rc;  // not a property of the plan
+      if (rc != CORTEX_OK) {
+        last_rc = rc;
+        continue;
+      }
+      ++tried;
+      if (best_ms < 0.0 || ms < best_ms) {
+        best_ms = ms;
+        *best = o;
+      }
+    }
+  if (n_tried) *n_tried = tried;
+  if (best_ms < 0.0) return fail(last_rc, "cortex_autotune: no candidate plan could be built");
+  if (best_ms_per_step) *best_ms_per_step = best_ms / trial_steps;
+  return CORTEX_OK;
 }
 
 int cortex_simulate(cortex_net* h, int64_t n_steps) {

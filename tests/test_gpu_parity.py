@@ -188,3 +188,22 @@ def test_deliver_counts_out_degree(cortex):
     outdeg = np.bincount(src, minlength=spec.n)
     assert ev == int(outdeg[ids].sum())
     assert ms > 0
+
+
+def test_autotune_plan_does_not_change_results(cortex):
+    """The autotuner times candidate plans (warps per block x block balance).  Every plan gives the
+    same rasters, because the summation order does not depend on the partition, and the oracle's."""
+    specs, seeds = W.small_batch_specs()
+    best, ms, n = cortex.autotune(specs, seeds, trial_steps=200)
+    assert n >= 2 and ms > 0
+    assert best.warps_per_block in (8, 10, 12, 14) and best.balance in (0, 1)
+    rasters = []
+    for opts in (best, cortex.make_options(warps_per_block=8, balance=1), cortex.make_options()):
+        with cortex.Network(specs, seeds, opts) as net:
+            net.simulate(600)
+            rasters.append([net.spikes(b) for b in range(len(specs))])
+    for r in rasters[1:]:
+        for (s0, i0), (s1, i1) in zip(rasters[0], r):
+            assert np.array_equal(s0, s1) and np.array_equal(i0, i1)
+    _, os_, oi, _ = oracle_run(specs[0], seeds[0], 600)
+    assert first_mismatch(*rasters[0][0], os_, oi) == -1
