@@ -125,6 +125,8 @@ int validate_params(const cortex_params& p, std::string& why) {
   if (!(p.tau_m > 0) || !(p.tau_syn > 0) || !(p.c_m > 0) || !(p.dt > 0) || !(p.t_ref >= 0))
     return why = "time constants, capacitance, dt and t_ref must be positive", CORTEX_ERR_ARG;
   if (p.tau_m == p.tau_syn) return why = "tau_m == tau_syn (singular propagator)", CORTEX_ERR_UNSUPPORTED;
+  if (std::llround((double)p.t_ref / (double)p.dt) > 32767)
+    return why = "t_ref / dt above 32767 steps (16-bit refractory counter)", CORTEX_ERR_UNSUPPORTED;
   if (!(p.nu_ext_hz >= 0)) return why = "nu_ext_hz", CORTEX_ERR_ARG;
   if (p.weight_dtype != CORTEX_F32 && p.weight_dtype != CORTEX_BF16) return why = "weight_dtype", CORTEX_ERR_ARG;
   if (p.e_l != 0.0f) return why = "only E_L = 0 is supported (potentials relative to rest)", CORTEX_ERR_UNSUPPORTED;

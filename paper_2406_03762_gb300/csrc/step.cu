@@ -26,6 +26,8 @@
 // round r + kStages - 1 into shared memory with 16-byte cp.async copies (each spike has a
 // fixed-size region of its slot), then fold round r; the headers of round r + kStages load into
 // registers meanwhile.  So kStages - 1 rounds of records are always in flight.
+#include <type_traits>
+
 #include "cortex_internal.cuh"
 
 namespace cortex {
@@ -51,8 +53,8 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   o += max_nt * 4;
   L.si = o;
   o += max_nt * 4;
-  L.sr = o;
-  o += max_nt * 4;
+  L.sr = o;    // refractory counters (32 bit; 16 bit when the ring is global, to leave room for staging)
+  o += max_nt * (ring_smem ? 4 : 2);
   o = align_to(o, 16);
   L.thr = o;
   o += kPoissonCap * 4;
@@ -65,8 +67,8 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   L.wcnt = o;
   o += (kMaxWarps + 2) * 4;
   o = align_to(o, 16);
-  L.wlist = o;
-  o += max_nt * 4;
+  L.wlist = o;  // per-warp spike lists of a step (local ids; 32 bit, 16 bit when the ring is global)
+  o += max_nt * (ring_smem ? 4 : 2);
   o = align_to(o, 16);
   L.ids = o;
   o += kIdCap * 4;
@@ -199,6 +201,9 @@ __device__ __forceinline__ void fold_chunk(float* ring, uint8_t* wtags, uint32_t
 template <bool kRingSmem, bool kBf16>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   constexpr uint32_t kWsz = kBf16 ? 2u : 4u;  // bytes per stored weight
+  // neuron chunks per update iteration: a global ring is read from L2, so several reads are kept
+  // in flight; a shared ring is read with low latency and small per-warp ranges favour one
+  constexpr int kUpd = kRingSmem ? 1 : 4;
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
   const int blk = blockIdx.x;
@@ -232,12 +237,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   float* ring_s = reinterpret_cast<float*>(smem + L.ring);
   float* sV = reinterpret_cast<float*>(smem + L.sv);
   float* sI = reinterpret_cast<float*>(smem + L.si);
-  int32_t* sR = reinterpret_cast<int32_t*>(smem + L.sr);
+  using RefT = typename std::conditional<kRingSmem, int32_t, int16_t>::type;
+  using ListT = typename std::conditional<kRingSmem, uint32_t, uint16_t>::type;
+  RefT* sR = reinterpret_cast<RefT*>(smem + L.sr);
   uint32_t* thr = reinterpret_cast<uint32_t*>(smem + L.thr);
   uint32_t* cnt_s = reinterpret_cast<uint32_t*>(smem + L.cnt);
   uint32_t* woffs = reinterpret_cast<uint32_t*>(smem + L.woffs);
   uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + L.wcnt);
-  uint32_t* wlist = reinterpret_cast<uint32_t*>(smem + L.wlist);
+  ListT* wlist = reinterpret_cast<ListT*>(smem + L.wlist);
   uint32_t* ids_s = reinterpret_cast<uint32_t*>(smem + L.ids);
   unsigned long long* mbl = reinterpret_cast<unsigned long long*>(smem + L.mbl);
   uint16_t* mbi = reinterpret_cast<uint16_t*>(smem + L.mbi);
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
     for (int j = tid; j < nt; j += blockDim.x) {
       sV[j] = a.V[nbase + j];
       sI[j] = a.I[nbase + j];
-      sR[j] = a.R[nbase + j];
+      sR[j] = (RefT)a.R[nbase + j];
     }
   }
   if (kRingSmem) {
@@ -274,11 +281,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
 
   // Poisson counts of steps tfirst .. tfirst + ns - 1 for every owned target (elements q0, q0 + dq, ...)
   auto poisson_fill = [&](long long tfirst, int ns, int q0, int dq) {
-    for (int q = q0; q < ns * nt; q += dq) {
-      const int sidx = q / nt, j = q - sidx * nt;
-      const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)(tfirst + sidx), kStreamPoisson, 0u),
+    const int tot = ns * nt;
+    if (kRingSmem) {
+      for (int q = q0; q < tot; q += dq) {
+        const int sidx = q / nt, j = q - sidx * nt;
+        const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)(tfirst + sidx), kStreamPoisson, 0u),
+                                       seed_lo, seed_hi);
+        pk[sidx * nt + j] = (uint8_t)poisson_k(rr.x, nd, thr);
+      }
+      return;
+    }
+    for (int q = q0; q < tot; q += 2 * dq) {  // large blocks: two independent generator calls per iteration
+      const int q2 = q + dq;
+      const int s1 = q / nt, j1 = q - s1 * nt;
+      const int s2 = (q2 < tot ? q2 : q) / nt, j2 = (q2 < tot ? q2 : q) - s2 * nt;
+      const uint4 r1 = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j1), (uint32_t)(tfirst + s1), kStreamPoisson, 0u),
                                      seed_lo, seed_hi);
-      pk[sidx * nt + j] = (uint8_t)poisson_k(rr.x, nd, thr);
+      const uint4 r2 = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j2), (uint32_t)(tfirst + s2), kStreamPoisson, 0u),
+                                     seed_lo, seed_hi);
+      pk[s1 * nt + j1] = (uint8_t)poisson_k(r1.x, nd, thr);
+      if (q2 < tot) pk[s2 * nt + j2] = (uint8_t)poisson_k(r2.x, nd, thr);
     }
   };
   const bool defer = persistent;  // V/I halves with the window's last I half after the barrier
@@ -311,33 +333,85 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         const uint32_t tu = (uint32_t)(defer ? t - 1 : t);
         const int lo = warp * tw_u, hi = min(lo + tw_u, nt);
         uint32_t cw = 0;
-        for (int c = lo; c < hi; c += 32) {
-          const int j = c + lane;
-          bool spk = false;
-          if (j < hi) {
-            float v = sV[j], cur = sI[j];
-            int32_t r = sR[j];
-            if (defer) {
-              if (prev) {
+        if constexpr (kUpd == 1) {
+          for (int c = lo; c < hi; c += 32) {
+            const int j = c + lane;
+            bool spk = false;
+            if (j < hi) {
+              float v = sV[j], cur = sI[j];
+              int32_t r = sR[j];
+              if (defer) {
+                if (prev) {
+                  const float in = ring_read<kRingSmem>(rs + j);
+                  rs[j] = 0.0f;
+                  i_half_k(cur, in, pk[ws * nt + j], nd);
+                }
+                spk = v_half(v, cur, r, nd);
+              } else {
                 const float in = ring_read<kRingSmem>(rs + j);
                 rs[j] = 0.0f;
-                i_half_k(cur, in, pk[ws * nt + j], nd);
+                const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+                spk = v_half(v, cur, r, nd);
+                i_half(cur, in, rr.x, nd, thr);
               }
-              spk = v_half(v, cur, r, nd);
-            } else {
-              const float in = ring_read<kRingSmem>(rs + j);
-              rs[j] = 0.0f;
-              const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
-              spk = v_half(v, cur, r, nd);
-              i_half(cur, in, rr.x, nd, thr);
+              sV[j] = v;
+              sI[j] = cur;
+              sR[j] = (RefT)r;
             }
-            sV[j] = v;
-            sI[j] = cur;
-            sR[j] = r;
+            const uint32_t bal = __ballot_sync(0xffffffffu, spk);
+            if (spk) wlist[lo + cw + __popc(bal & lanemask_lt())] = (ListT)j;
+            cw += __popc(bal);
           }
-        const uint32_t bal = __ballot_sync(0xffffffffu, spk);
-          if (spk) wlist[lo + cw + __popc(bal & lanemask_lt())] = (uint32_t)(wk.t0 + j);
-          cw += __popc(bal);
+        } else {
+        for (int c = lo; c < hi; c += kUpd * 32) {
+          // kUpd 32-neuron chunks: their loads are issued together, then updated, then compacted
+          // in ascending order
+          float v[kUpd], cur[kUpd], in[kUpd];
+          int32_t r[kUpd];
+          int kp[kUpd];
+#pragma unroll
+          for (int u = 0; u < kUpd; ++u) {
+            const int j = c + 32 * u + lane;
+            in[u] = 0.0f;
+            kp[u] = 0;
+            if (j < hi) {
+              v[u] = sV[j];
+              cur[u] = sI[j];
+              r[u] = sR[j];
+              if (!defer || prev) in[u] = ring_read<kRingSmem>(rs + j);
+              if (defer && prev) kp[u] = pk[ws * nt + j];
+            }
+          }
+          bool spk[kUpd];
+#pragma unroll
+          for (int u = 0; u < kUpd; ++u) {
+            const int j = c + 32 * u + lane;
+            spk[u] = false;
+            if (j < hi) {
+              if (defer) {
+                if (prev) {
+                  rs[j] = 0.0f;
+                  i_half_k(cur[u], in[u], kp[u], nd);
+                }
+                spk[u] = v_half(v[u], cur[u], r[u], nd);
+              } else {
+                rs[j] = 0.0f;
+                const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+                spk[u] = v_half(v[u], cur[u], r[u], nd);
+                i_half(cur[u], in[u], rr.x, nd, thr);
+              }
+              sV[j] = v[u];
+              sI[j] = cur[u];
+              sR[j] = (RefT)r[u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kUpd; ++u) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, spk[u]);
+            if (spk[u]) wlist[lo + cw + __popc(bal & lanemask_lt())] = (ListT)(c + 32 * u + lane);
+            cw += __popc(bal);
+          }
+        }
         }
         if (lane == 0) wcnt[warp] = cw;
         __syncthreads();
@@ -349,7 +423,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         }
         uint32_t* dst = a.pub_ids + ((int64_t)(par * a.w_max + ws) * a.n_total + neuron_base + wk.t0);
         for (uint32_t q = lane; q < cw; q += 32) {
-          const uint32_t id = wlist[lo + q];
+          const uint32_t id = (uint32_t)wk.t0 + wlist[lo + q];
           dst[before + q] = id;
           const uint32_t pw = win_total + before + q;
           if (persistent && pw < inl) mbi[pw] = (uint16_t)(id - (uint32_t)wk.t0);
