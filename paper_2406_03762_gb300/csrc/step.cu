@@ -39,7 +39,8 @@ struct SmemLayout {
 __host__ __device__ inline uint32_t align_to(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 // duplicate-detection tags: one byte per ring cell when the ring is in shared memory, else a
-// hashed table of kTagHash bytes per warp
+// hashed table of kTagHash bytes per warp.  (Finding the sharing of several chunks ahead of their
+// ring updates, in separate tables, measured slower with reductions into a global ring.)
 constexpr int kTagHash = 2048;
 
 __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int w_max, int max_nb, bool ring_smem,
@@ -161,36 +162,73 @@ __device__ __forceinline__ float ring_read(const float* p) {
   return __ldcg(p);
 }
 
-// Add the weights of one 32-lane chunk to their ring cells (key = cell, 0xffffffff = no entry).
-// Lanes hold entries in stream order.  Lanes whose cell no other lane of the chunk touches add at
-// once; lanes that share a cell add one by one in lane order, so every cell folds its weights in
-// stream order.  Sharing is found by writing the lane id into a tag per cell and reading it back.
+// Ring updates of one 32-lane chunk (key = cell, 0xffffffff = no entry) whose sharing is known:
+// t = the lane id read back from the cell's tag, losers = lanes whose tag names another lane (a
+// group of lanes with one cell has one recorded writer; the others are losers).  Lanes hold
+// entries in stream order, and every cell must receive its weights in lane order:
+//   - no sharing: all lanes add at once;
+//   - every group a pair (one loser, one writer): the lower lane of each pair adds with the
+//     unshared lanes, then the higher lanes add;
+//   - otherwise: unshared lanes at once, then the shared lanes one by one in lane order.
+// With hashed tags two lanes of different cells may be taken for a pair: they are then merely
+// ordered, which is always allowed.
 template <bool kRingSmem>
-__device__ __forceinline__ void fold_chunk(float* ring, uint8_t* wtags, uint32_t key, float w, int lane, bool red) {
+__device__ __forceinline__ void fold_apply(float* ring, uint32_t key, float w, uint32_t t, uint32_t losers, int lane,
+                                           bool red) {
   const bool valid = key != 0xffffffffu;
-  // shared ring: one tag per cell (warps own disjoint cells); global ring: the warp's hashed table
-  uint8_t* tg = kRingSmem ? wtags + (valid ? key : 0u) : wtags + (key & (uint32_t)(kTagHash - 1));
-  if (valid) *tg = (uint8_t)lane;
-  __syncwarp();
-  const uint32_t t = valid ? (uint32_t)*tg : (uint32_t)lane;
-  const bool loser = valid && t != (uint32_t)lane;
-  const uint32_t losers = __ballot_sync(0xffffffffu, loser);
   if (losers == 0) {
     if (valid) ring_add<kRingSmem>(ring, key, w, red);
-  } else {
-    const uint32_t winners = __reduce_or_sync(0xffffffffu, loser ? (1u << t) : 0u);
-    const uint32_t dup = losers | winners;
-    if (valid && !((dup >> lane) & 1u)) ring_add<kRingSmem>(ring, key, w, red);
     __syncwarp();
-    uint32_t m = dup;
-    while (m) {
-      const int first = __ffs(m) - 1;
-      if (lane == first) ring_add<kRingSmem>(ring, key, w, red);
-      __syncwarp();
-      m &= m - 1u;
-    }
+    return;
+  }
+  const bool loser = (losers >> lane) & 1u;
+  const uint32_t winners = __reduce_or_sync(0xffffffffu, loser ? (1u << t) : 0u);
+  const uint32_t wfirst = __reduce_or_sync(0xffffffffu, (loser && (uint32_t)lane > t) ? (1u << t) : 0u);
+  const uint32_t dup = losers | winners;
+  const bool isdup = (dup >> lane) & 1u;
+  if (__popc(losers) == __popc(winners)) {
+    const bool first = !isdup || (loser ? ((uint32_t)lane < t) : ((wfirst >> lane) & 1u));
+    if (valid && first) ring_add<kRingSmem>(ring, key, w, red);
+    __syncwarp();
+    if (valid && !first) ring_add<kRingSmem>(ring, key, w, red);
+    __syncwarp();
+    return;
+  }
+  if (valid && !isdup) ring_add<kRingSmem>(ring, key, w, red);
+  __syncwarp();
+  uint32_t m = dup;
+  while (m) {
+    const int f = __ffs(m) - 1;
+    if (lane == f) ring_add<kRingSmem>(ring, key, w, red);
+    __syncwarp();
+    m &= m - 1u;
+  }
+}
+
+// Fold G consecutive chunks: the sharing of all G is found first (each chunk writes its lane ids
+// into its own tag array and reads them back), then the ring updates run chunk after chunk.
+// Shared ring: one tag per cell (warps own disjoint cells).  Global ring: hashed tag arrays of
+// kTagHash bytes per warp.  The kernel folds one chunk per group (G = 1).
+template <bool kRingSmem, int G>
+__device__ __forceinline__ void fold_group(float* ring, uint8_t* wtags, const uint32_t* key, const float* w, int lane,
+                                           bool red) {
+  uint8_t* tg[G];
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    const bool valid = key[u] != 0xffffffffu;
+    tg[u] = kRingSmem ? wtags + (valid ? key[u] : 0u) : wtags + u * kTagHash + (key[u] & (uint32_t)(kTagHash - 1));
+    if (valid) *tg[u] = (uint8_t)lane;
   }
   __syncwarp();
+  uint32_t t[G], losers[G];
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    const bool valid = key[u] != 0xffffffffu;
+    t[u] = valid ? (uint32_t)*tg[u] : (uint32_t)lane;
+    losers[u] = __ballot_sync(0xffffffffu, valid && t[u] != (uint32_t)lane);
+  }
+#pragma unroll
+  for (int u = 0; u < G; ++u) fold_apply<kRingSmem>(ring, key[u], w[u], t[u], losers[u], lane, red);
 }
 
 // ---- the step kernel ---------------------------------------------------------------------------
@@ -823,12 +861,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) fold_chunk<kRingSmem>(ring, wtags, key[u], wv[u], lane, ring_red);
+            for (int u = 0; u < 4; ++u) fold_group<kRingSmem, 1>(ring, wtags, key + u, wv + u, lane, ring_red);
           }
           for (; e < total; e += 32) {
             float wv;
             const uint32_t key = chunk_key(e, wv);
-            fold_chunk<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
+            fold_group<kRingSmem, 1>(ring, wtags, &key, &wv, lane, ring_red);
           }
         }
         __syncthreads();
