@@ -198,12 +198,14 @@ static uint32_t v0_word(uint64_t seed, int64_t i) {
   return r[0];
 }
 
+/* External drive of neuron i at step t: word (i mod 4) of Philox(ctr = (floor(i / 4), t,
+ * STREAM_POISSON, 0)); one generator call serves four consecutive neurons at one step. */
 static uint32_t poisson_word(uint64_t seed, int64_t i, int64_t t) {
-  uint32_t ctr[4] = {(uint32_t)i, (uint32_t)t, STREAM_POISSON, 0u};
+  uint32_t ctr[4] = {(uint32_t)(i >> 2), (uint32_t)t, STREAM_POISSON, 0u};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t r[4];
   oracle_philox4x32_10(ctr, key, r);
-  return r[0];
+  return r[i & 3];
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -641,13 +643,13 @@ void oracle_set_state(oracle_net* net, const double* v, const double* cur, const
  * spike of step t is delivered onto the chosen targets (deliver(), same order as the full
  * simulation).  The targets' own spikes are written to out_step/out_id (up to cap; *out_n is the
  * count, which may exceed cap) and their final V, I, refractory counts to v/cur/refr (widened to
- * double).  The raster is taken as given: a target's own replayed spikes are not fed back, so a
+ * double); v_trace (optional, [n_steps][n_t]) receives every target's V after every step.  The raster is taken as given: a target's own replayed spikes are not fed back, so a
  * run of the full oracle replays to itself exactly, and a raster from another simulator is
  * checked one target at a time. */
 int oracle_replay(const oracle_params* p, uint64_t seed, int64_t n_t, const int32_t* targets,
                   int64_t n_steps, int64_t n_spk, const int64_t* spk_step, const int32_t* spk_id,
                   int64_t cap, int64_t* out_step, int32_t* out_id, int64_t* out_n,
-                  double* v, double* cur, int32_t* refr) {
+                  double* v, double* cur, int32_t* refr, double* v_trace) {
   if (!validate(p) || n_t < 0 || n_steps < 0 || n_spk < 0 || cap < 0 || !out_n) return ORACLE_ERR_ARG;
   const int64_t n = (int64_t)p->n_exc + p->n_inh;
   for (int64_t q = 0; q < n_t; ++q)
@@ -692,6 +694,8 @@ int oracle_replay(const oracle_params* p, uint64_t seed, int64_t n_t, const int3
         if (got < cap) { out_step[got] = t; out_id[got] = targets[q]; }
         ++got;
       }
+      if (v_trace)
+        v_trace[t * n_t + q] = (p->precision == ORACLE_FP32) ? (double)net->v32[targets[q]] : net->v64[targets[q]];
     }
     while (e < n_spk && spk_step[e] < t) ++e;
     while (e < n_spk && spk_step[e] == t) { deliver(net, spk_id[e], t); ++e; }

@@ -125,7 +125,7 @@ def lib():
         L.oracle_replay.argtypes = [P(_Params), ctypes.c_uint64, ctypes.c_int64, P(ctypes.c_int32), ctypes.c_int64,
                                     ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int32), ctypes.c_int64,
                                     P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_double),
-                                    P(ctypes.c_double), P(ctypes.c_int32)]
+                                    P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_double)]
         L.oracle_replay.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -227,11 +227,11 @@ def poisson_word(seed: int, i: int, t: int) -> int:
     return int(lib().oracle_poisson_word(seed, i, t))
 
 
-def replay(p: Params, seed: int, targets, n_steps: int, raster_steps, raster_ids):
+def replay(p: Params, seed: int, targets, n_steps: int, raster_steps, raster_ids, trace: bool = False):
     """Simulate only the given targets of the Philox network, driven by a given raster of the whole
     network (its (step, id) pairs sorted by step, then id).  Returns (spike steps, spike ids) of the
     targets, in (step, id) order, and their final (V, I, refractory count) as arrays in target
-    order.  A target's trajectory depends only on its own incoming synapses and the raster, so
+    order; with trace=True also V of every target after every step ([n_steps, targets]).  A target's trajectory depends only on its own incoming synapses and the raster, so
     this checks a large simulation one neuron at a time."""
     t = np.ascontiguousarray(np.unique(np.asarray(targets, dtype=np.int32)))
     rs = np.ascontiguousarray(np.asarray(raster_steps, dtype=np.int64))
@@ -244,14 +244,18 @@ def replay(p: Params, seed: int, targets, n_steps: int, raster_steps, raster_ids
         v = np.empty(len(t), dtype=np.float64)
         c = np.empty(len(t), dtype=np.float64)
         r = np.empty(len(t), dtype=np.int32)
+        tr = np.empty((n_steps, len(t)), dtype=np.float64) if trace else None
         pc = p.c()
         rc = lib().oracle_replay(ctypes.byref(pc), seed, len(t), _ptr(t, ctypes.c_int32), n_steps, len(rs),
                                  _ptr(rs, ctypes.c_int64), _ptr(ri, ctypes.c_int32), cap,
                                  _ptr(os_, ctypes.c_int64), _ptr(oi, ctypes.c_int32), ctypes.byref(n_out),
-                                 _ptr(v, ctypes.c_double), _ptr(c, ctypes.c_double), _ptr(r, ctypes.c_int32))
+                                 _ptr(v, ctypes.c_double), _ptr(c, ctypes.c_double), _ptr(r, ctypes.c_int32),
+                                 _ptr(tr, ctypes.c_double) if trace else None)
         if rc != 0:
             raise RuntimeError(f"oracle_replay failed ({rc})")
         if n_out.value <= cap:
+            if trace:
+                return os_[:n_out.value], oi[:n_out.value], (v, c, r), tr
             return os_[:n_out.value], oi[:n_out.value], (v, c, r)
         cap = int(n_out.value)
 

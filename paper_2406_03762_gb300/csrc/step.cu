@@ -100,7 +100,8 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
 // ---- one neuron, one step (Eq. 1-3, exact integration) --------------------------------------
 //   V half: refractory: V = V_reset, counter - 1;  else V = V + fma(P22 - 1, V, P21 * I) with
 //           the I of the previous step;  V >= V_th: spike, V = V_reset, counter = n_ref (Eq. 2)
-//   I half: in = ring cell of the step (cleared); k = Poisson draw; ext = k * J_ext;
+//   I half: in = ring cell of the step (cleared); k = Poisson draw (neuron i, step t: word i mod 4
+//           of Philox(counter = (i / 4, t, 3, 0))); ext = k * J_ext;
 //           I = fma(P11, I, in); I = I + ext
 struct NeuronConst {
   float p11, p21, p22m1, v_th, v_reset, j_ext;
@@ -120,6 +121,11 @@ __device__ __forceinline__ bool v_half(float& v, float cur, int32_t& r, const Ne
     r = nd.n_ref;
   }
   return spk;
+}
+
+// word w (0..3) of a generator output
+__device__ __forceinline__ uint32_t philox_word(const uint4& r, uint32_t w) {
+  return w == 0u ? r.x : (w == 1u ? r.y : (w == 2u ? r.z : r.w));
 }
 
 // Poisson count of the external drive by inversion: the smallest k with u < thr[k]
@@ -317,28 +323,36 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   bool aborted = false;
   __syncthreads();
 
-  // Poisson counts of steps tfirst .. tfirst + ns - 1 for every owned target (elements q0, q0 + dq, ...)
-  auto poisson_fill = [&](long long tfirst, int ns, int q0, int dq) {
-    const int tot = ns * nt;
-    if (kRingSmem) {
-      for (int q = q0; q < tot; q += dq) {
-        const int sidx = q / nt, j = q - sidx * nt;
-        const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), (uint32_t)(tfirst + sidx), kStreamPoisson, 0u),
-                                       seed_lo, seed_hi);
-        pk[sidx * nt + j] = (uint8_t)poisson_k(rr.x, nd, thr);
+  // Poisson counts of steps tfirst .. tfirst + ns - 1 for every owned target.  One generator call
+  // gives the drive of four consecutive neurons (network-local ids 4g .. 4g + 3) at one step; the
+  // work items are (step, group of four) pairs q0, q0 + dq, ...
+  const int pq_g0 = wk.t0 >> 2, pq_ng = ((wk.t0 + nt + 3) >> 2) - pq_g0;  // groups of four targets
+  auto poisson_fill = [&](long long tfirst, int ns, int q0, int qend, int dq) {
+    const int g0 = pq_g0, ng = pq_ng;
+    const int tot = min(ns * ng, qend);
+    for (int q = q0; q < tot; q += dq) {
+      const int sidx = q / ng, g = g0 + (q - sidx * ng);
+      const uint4 rr = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(tfirst + sidx), kStreamPoisson, 0u),
+                                     seed_lo, seed_hi);
+      const uint32_t wd[4] = {rr.x, rr.y, rr.z, rr.w};
+      // the four inversions side by side: threshold k is read once for all words still above it
+      int kk[4] = {0, 0, 0, 0};
+      for (int k = 0; k < nd.n_thr - 1; ++k) {
+        const uint32_t th = thr[k];
+        bool any = false;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const bool up = kk[w] == k && wd[w] >= th;
+          kk[w] += up ? 1 : 0;
+          any = any || up;
+        }
+        if (!any) break;
       }
-      return;
-    }
-    for (int q = q0; q < tot; q += 2 * dq) {  // large blocks: two independent generator calls per iteration
-      const int q2 = q + dq;
-      const int s1 = q / nt, j1 = q - s1 * nt;
-      const int s2 = (q2 < tot ? q2 : q) / nt, j2 = (q2 < tot ? q2 : q) - s2 * nt;
-      const uint4 r1 = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j1), (uint32_t)(tfirst + s1), kStreamPoisson, 0u),
-                                     seed_lo, seed_hi);
-      const uint4 r2 = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j2), (uint32_t)(tfirst + s2), kStreamPoisson, 0u),
-                                     seed_lo, seed_hi);
-      pk[s1 * nt + j1] = (uint8_t)poisson_k(r1.x, nd, thr);
-      if (q2 < tot) pk[s2 * nt + j2] = (uint8_t)poisson_k(r2.x, nd, thr);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int j = 4 * g + w - wk.t0;
+        if (j >= 0 && j < nt) pk[sidx * nt + j] = (uint8_t)kk[w];
+      }
     }
   };
   const bool defer = persistent;  // V/I halves with the window's last I half after the barrier
@@ -346,7 +360,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   const int W = persistent ? window : min(window, a.n_steps);
   if (persistent && do_update) {
     // the first window's table: pk[s] holds step t_start - 1 + s (the I half run before V half s)
-    poisson_fill(t_start - 1, min(W, a.n_steps), tid, blockDim.x);
+    poisson_fill(t_start - 1, min(W, a.n_steps), tid, 1 << 30, blockDim.x);
     __syncthreads();
   }
   const int tw_u = (nt + n_warps - 1) / n_warps;  // update split over the warps
@@ -388,9 +402,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
               } else {
                 const float in = ring_read<kRingSmem>(rs + j);
                 rs[j] = 0.0f;
-                const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+                const uint32_t gi = (uint32_t)(wk.t0 + j);
+                const uint4 rr = philox4x32_10(make_uint4(gi >> 2, tu, kStreamPoisson, 0u), seed_lo, seed_hi);
                 spk = v_half(v, cur, r, nd);
-                i_half(cur, in, rr.x, nd, thr);
+                i_half(cur, in, philox_word(rr, gi & 3u), nd, thr);
               }
               sV[j] = v;
               sI[j] = cur;
@@ -434,9 +449,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
                 spk[u] = v_half(v[u], cur[u], r[u], nd);
               } else {
                 rs[j] = 0.0f;
-                const uint4 rr = philox4x32_10(make_uint4((uint32_t)(wk.t0 + j), tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+                const uint32_t gi = (uint32_t)(wk.t0 + j);
+                const uint4 rr = philox4x32_10(make_uint4(gi >> 2, tu, kStreamPoisson, 0u), seed_lo, seed_hi);
                 spk[u] = v_half(v[u], cur[u], r[u], nd);
-                i_half(cur[u], in[u], rr.x, nd, thr);
+                i_half(cur[u], in[u], philox_word(rr, gi & 3u), nd, thr);
               }
               sV[j] = v[u];
               sI[j] = cur[u];
@@ -478,8 +494,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         // Publication: the block's mailbox line for this window.  Every 64-bit word carries the
         // window's tag in its top 16 bits, so a reader that sees the tag in a word sees that word's
         // payload: count words (three u16 step counts each), then id words (three u16 local ids
-        // each).  The fence orders the global id lists (read by others only beyond the line's
-        // capacity) before the words.
+        // each).  The count words are release stores: they order the global id lists
+        // (read by others only beyond the line's capacity) before them.
         const unsigned long long tag = (unsigned long long)(((epoch + 1u) & 0x7fffu) | 0x8000u) << 48;
         const uint32_t nin = min(win_total, inl);
         if (tid < kMboxWords && blk != a.withhold_block) {
@@ -493,8 +509,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
               if (pq < nin) pay |= (unsigned long long)mbi[pq] << (16 * f);
             }
           }
-          __threadfence();
-          st_relaxed_u64(a.mbox + ((size_t)par * a.n_blocks + blk) * kMboxWords + tid, tag | pay);
+          unsigned long long* dst = a.mbox + ((size_t)par * a.n_blocks + blk) * kMboxWords + tid;
+          if (tid < n_cw) st_release_u64(dst, tag | pay);  // after the block's global id lists
+          else st_relaxed_u64(dst, tag | pay);
         }
         // L2 prefetch of the spiking rows (every block of the network reads them after the
         // barrier): the header row and the record rows of the window's first spikes
@@ -573,12 +590,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
       // the next window's Poisson table (its first entry is this window's last step, whose I half
       // runs after the delivery): threads that do not poll fill it meanwhile
       if (do_update) {
-        const int wn_next = min(W, a.n_steps - done - Wn);
-        const int ns = max(wn_next, 1);
+        const int ns = max(min(W, a.n_steps - done - Wn), 1);
         if ((int)blockDim.x > nb) {
-          if (tid >= nb) poisson_fill(t0 + Wn - 1, ns, tid - nb, (int)blockDim.x - nb);
+          if (tid >= nb) poisson_fill(t0 + Wn - 1, ns, tid - nb, 1 << 30, (int)blockDim.x - nb);
         } else {
-          poisson_fill(t0 + Wn - 1, ns, tid, blockDim.x);
+          poisson_fill(t0 + Wn - 1, ns, tid, 1 << 30, blockDim.x);
         }
       }
       if (__syncthreads_or(fail)) {

@@ -7,14 +7,14 @@ target's spikes and final (V, I, refractory count) must equal the GPU's bit for 
 launch configuration is the one the benchmark times (persistent kernel, 1000 steps per launch,
 default warps per block).
 
-Precision (FP32 state and accumulation): potentials within 1e-6 of the FP64 oracle relative to
-max(|V64|, V_th) until the rasters first differ, population rates within 1% (or the 3-sigma band
-of the rate fluctuations) after that.  BF16 weights: rates against the FP64 oracle on the
+Precision (FP32 state and accumulation): potentials within 1e-6 of the FP64 oracle, relative to
+max(|V64|, V_th), with the FP64 oracle driven by the GPU's own raster; population rates within 1%
+(or the 3-sigma band of the rate fluctuations) of the free-running FP64 oracle.  BF16 weights: rates against the FP64 oracle on the
 10,000-neuron network with the statistics of the 1e6-neuron configuration (K = 11,250)."""
 import numpy as np
 import pytest
 
-from helpers import first_mismatch, oracle_params, oracle_run
+from helpers import first_mismatch, fp64_replay_check, oracle_params, oracle_run
 from oracle import oracle as orc
 from paper_2406_03762_gb300 import workloads as W
 
@@ -104,8 +104,11 @@ def _rate_check(spec, s_a, i_a, s_b, i_b, t0, t1, block=250):
 
 
 def test_fp32_potentials_and_rates_against_fp64_oracle(cortex):
-    """N = 2,500: V of every neuron after every step of the first 100 ms within 1e-6 of the FP64
-    oracle (relative to max(|V64|, V_th)) while the rasters agree; rates over 200 ms."""
+    """N = 2,500, FP32 on the GPU against the FP64 oracle.
+    Potentials: every neuron after every step of the first 100 ms within 1e-6 of the FP64 oracle
+    replaying that neuron with the GPU's raster as presynaptic input, relative to max(|V64|, V_th),
+    up to the neuron's own first spike-time difference.
+    Rates: the free-running FP64 oracle over 200 ms, after its raster first departs from the GPU's."""
     cfg = W.CONFIGS["c0"]
     spec, seed, steps = cfg["spec"], cfg["seed"], cfg["steps"]
     n_v = 1000
@@ -116,16 +119,13 @@ def test_fp32_potentials_and_rates_against_fp64_oracle(cortex):
             gv[t] = net.state()[0]
         net.simulate(steps - n_v)
         gs, gi = net.spikes()
-    ref, os_, oi, tr = oracle_run(spec, seed, steps, precision=orc.FP64,
-                                  trace_ids=np.arange(spec.n, dtype=np.int32))
-    v64 = tr[:n_v]
+    err, agree = fp64_replay_check(spec, seed, n_v, gs, gi, gv)
+    assert agree >= 0.99, f"only {agree:.4f} of the neurons keep their spike times"
+    assert err <= 1e-6, f"max relative V error {err:.3g}"
+    _, os_, oi, _ = oracle_run(spec, seed, steps, precision=orc.FP64)
     fm = first_mismatch(gs, gi, os_, oi)
-    t_star = int(min(gs[fm], os_[fm])) if 0 <= fm < min(len(gs), len(os_)) else (steps if fm == -1 else int(gs[-1]))
-    t_v = min(t_star, n_v)
-    assert t_v >= 500, f"rasters differ from step {t_star}"
-    err = np.abs(gv[:t_v] - v64[:t_v]) / np.maximum(np.abs(v64[:t_v]), spec.v_th)
-    assert err.max() <= 1e-6, f"max relative V error {err.max():.3g}"
-    if t_star < steps:
+    t_star = int(min(gs[fm], os_[fm])) if 0 <= fm < min(len(gs), len(os_)) else steps
+    if t_star < steps - 500:
         for rel, sig in _rate_check(spec, gs, gi, os_, oi, t_star, steps):
             assert abs(rel) <= max(0.01, 3 * sig)
 

@@ -125,21 +125,20 @@ def test_propagator_p22_minus_one_matches_its_series():
 
 
 def test_fp32_potentials_track_fp64_within_1e6():
-    """The FP32 update (V + fma(P22 - 1, V, P21 I)) stays within 1e-6 of the FP64 run, relative to
-    max(|V64|, V_th), on the N=2,500 Brunel network over 100 ms while the rasters agree."""
+    """The FP32 update (V + fma(P22 - 1, V, P21 I)) stays within 1e-6 of FP64, relative to
+    max(|V64|, V_th), for every neuron of the N=2,500 network over 100 ms: the FP64 oracle replays
+    each neuron driven by the FP32 run's raster, and a neuron is compared up to its own first
+    spike-time difference (almost never reached)."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from helpers import fp64_replay_check
     from paper_2406_03762_gb300 import workloads as W
     c0 = W.CONFIGS["c0"]
     spec, seed = c0["spec"], c0["seed"]
-    runs = []
-    for prec in (o.FP32, o.FP64):
-        d = {k: v for k, v in spec.as_dict().items() if k in o.Params.__dataclass_fields__}
-        net = o.Network(o.Params(precision=prec, **d), seed)
-        tr = net.simulate(1000, trace_ids=np.arange(spec.n, dtype=np.int32))
-        runs.append((tr.reshape(1000, spec.n), *net.raster()))
-    (v32, s32, i32), (v64, s64, i64) = runs
-    n = min(len(s32), len(s64))
-    bad = np.nonzero((s32[:n] != s64[:n]) | (i32[:n] != i64[:n]))[0]
-    t_star = int(s32[bad[0]]) if len(bad) else (1000 if len(s32) == len(s64) else int(s32[n - 1]))
-    assert t_star >= 500
-    err = np.abs(v32[:t_star] - v64[:t_star]) / np.maximum(np.abs(v64[:t_star]), spec.v_th)
-    assert err.max() <= 1e-6
+    d = {k: v for k, v in spec.as_dict().items() if k in o.Params.__dataclass_fields__}
+    net = o.Network(o.Params(precision=o.FP32, **d), seed)
+    v32 = net.simulate(1000, trace_ids=np.arange(spec.n, dtype=np.int32))
+    s32, i32 = net.raster()
+    err, agree = fp64_replay_check(spec, seed, 1000, s32, i32, v32)
+    assert agree >= 0.99
+    assert err <= 1e-6

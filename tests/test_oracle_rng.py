@@ -101,3 +101,17 @@ def test_bf16_rounding():
         b = np.array([y], np.float32).view(np.uint32)[0]
         assert b & 0xFFFF == 0
         assert abs(y - float(x)) <= abs(float(x)) * 2.0**-8
+
+
+def test_poisson_word_layout_and_independence_of_the_four_words():
+    """Neuron i at step t draws word i mod 4 of Philox(counter = (i / 4, t, 3, 0)); the four
+    neurons that share one generator call get uncorrelated drives."""
+    seed = 31
+    for i, t in [(0, 0), (5, 7), (4099, 12345), (2 ** 20 - 1, 99)]:
+        words = o.philox4x32_10([i // 4, t, 3, 0], [seed & 0xffffffff, seed >> 32])
+        assert o.poisson_word(seed, i, t) == int(words[i % 4])
+    thr = o.poisson_table(1.5)
+    ks = np.array([[o.poisson_sample(o.poisson_word(seed, 4 * g + w, t), thr) for w in range(4)]
+                   for g in range(8) for t in range(600)], dtype=np.float64)
+    c = np.corrcoef(ks.T)
+    assert np.all(np.abs(c[np.triu_indices(4, 1)]) < 0.05)
