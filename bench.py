@@ -33,6 +33,23 @@ UNIT = "events/s"
 BYTES_PER_EVENT = {0: 7, 1: 5}   # FP32: w 4 B + local target 2 B + delay 1 B; BF16: 2 + 2 + 1
 
 
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank's replica: every rank simulates its own network (weak scaling)."""
+    return int(base_seed) + 1000 * int(rank)
+
+
+def replica_aggregate(ms: float, events: float, dist, device: str = "cuda"):
+    """Whole-job numbers over the ranks: the slowest rank's time and the sum of the events
+    (no collective on the data path; one max and one sum after the timed region)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(events)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -197,7 +214,7 @@ def our_arm(args):
     spec = cfg["spec"]
     stream = torch.cuda.Stream()
     opts = cortex.make_options(steps_per_launch=args.steps_per_launch, warps_per_block=args.warps)
-    net = cortex.Network(spec, cfg["seed"] + 1000 * rank, opts, stream=stream)
+    net = cortex.Network(spec, replica_seed(cfg["seed"], rank), opts, stream=stream)
     st0 = net.stats()
 
     def barrier():
@@ -231,13 +248,7 @@ def our_arm(args):
     st = net.stats()
     events = st["events"] - e_before
     spikes = st["spikes"] - s_before
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    e = torch.tensor([float(events)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    events_all = float(e.item())
+    ms_max, events_all = replica_aggregate(ms, events, dist, "cuda")
     value = events_all / (ms_max * 1e-3)
     sim_s = args.steps * args.sim_steps * spec.dt * 1e-3
     rtf = (ms_max * 1e-3) / sim_s
