@@ -33,7 +33,7 @@
 namespace cortex {
 
 struct SmemLayout {
-  uint32_t ring, sv, si, sr, thr, cnt, woffs, wcnt, wlist, ids, mbl, mbi, mbc, pk, hdr, desc, perm, tags, stage, total;
+  uint32_t ring, sv, si, sr, thr, cnt, woffs, wcnt, wlist, ids, mbl, mbi, mbc, pk, hdr, desc, dsoa, perm, tags, stage, total;
 };
 
 __host__ __device__ inline uint32_t align_to(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -83,8 +83,10 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   o += align_to((uint32_t)(w_max * max_nt), 16);
   L.hdr = o;   // fetched headers: kHdrSlots rounds of (32-byte header, 8-byte row start, pad) per spike
   o += kHdrSlots * kSpikeBatch * 48;
-  L.desc = o;  // piece descriptors: kStages + 1 rounds of 64 bytes per spike
-  o += (kStages + 1) * kSpikeBatch * 64;
+  L.desc = o;  // piece descriptors, kStages + 1 rounds: 32 bytes per spike (copy), then per round
+  o += (kStages + 1) * kSpikeBatch * 32;  //   u32 aux[spike] and u16 end[warp][spike] (fold)
+  L.dsoa = o;
+  o += (kStages + 1) * kSpikeBatch * (4 + 2 * kMaxWarps);
   L.perm = o;
   o += kMaxWarps * 32;
   o = align_to(o, 16);
@@ -237,6 +239,36 @@ __device__ __forceinline__ void fold_group(float* ring, uint8_t* wtags, const ui
   for (int u = 0; u < G; ++u) fold_apply<kRingSmem>(ring, key[u], w[u], t[u], losers[u], lane, red);
 }
 
+// Fold four consecutive chunks with one tag array, software-pipelined: chunk u + 1 writes its
+// tags as soon as chunk u's tags have been read (its ballot has consumed them), so that the tag
+// round trip of chunk u + 1 overlaps the ring updates of chunk u.  The __syncwarp that ends
+// chunk u's updates also orders chunk u + 1's tag writes before its tag reads.
+template <bool kRingSmem>
+__device__ __forceinline__ void fold_four(float* ring, uint8_t* wtags, const uint32_t* key, const float* w, int lane,
+                                          bool red) {
+  auto tag_of = [&](uint32_t k) -> uint8_t* {
+    return kRingSmem ? wtags + (k != 0xffffffffu ? k : 0u) : wtags + (k & (uint32_t)(kTagHash - 1));
+  };
+  uint8_t* tg = tag_of(key[0]);
+  if (key[0] != 0xffffffffu) *tg = (uint8_t)lane;
+  __syncwarp();
+  uint32_t t = key[0] != 0xffffffffu ? (uint32_t)*tg : (uint32_t)lane;
+  uint32_t losers = __ballot_sync(0xffffffffu, key[0] != 0xffffffffu && t != (uint32_t)lane);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uint8_t* tgn = nullptr;
+    if (u < 3) {
+      tgn = tag_of(key[u + 1]);
+      if (key[u + 1] != 0xffffffffu) *tgn = (uint8_t)lane;
+    }
+    fold_apply<kRingSmem>(ring, key[u], w[u], t, losers, lane, red);  // ends with __syncwarp
+    if (u < 3) {
+      t = key[u + 1] != 0xffffffffu ? (uint32_t)*tgn : (uint32_t)lane;
+      losers = __ballot_sync(0xffffffffu, key[u + 1] != 0xffffffffu && t != (uint32_t)lane);
+    }
+  }
+}
+
 // ---- the step kernel ---------------------------------------------------------------------------
 // phases: kPhaseUpdate, kPhaseDeliver, and kPhaseBarrier for the persistent form (both phases and
 // a barrier per window inside one cooperative launch of n_steps steps).  kRingSmem: the block's
@@ -296,6 +328,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   uint8_t* pk = smem + L.pk;
   unsigned char* hdr_s = smem + L.hdr;
   uint4* desc_s = reinterpret_cast<uint4*>(smem + L.desc);
+  unsigned char* dsoa_s = smem + L.dsoa;
   uint8_t* perm = smem + L.perm + warp * 32;
   uint8_t* tags = smem + L.tags;
   unsigned char* stage = smem + L.stage;
@@ -713,11 +746,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         cp_async16(h + 16, hp + 1);
         cp_async8(h + 32, a.row_base + row_off + id);
       };
-      // piece descriptor of spike k of round x (64 bytes, one lane writes it):
-      //   [0] 16-byte-aligned global addresses of the weight and meta pieces
-      //   [1] x: weight chunks | meta chunks << 16; y: weight offset | meta offset << 8 | slot << 16
-      //   [2..3] the header's u16 end[w] (bytes 32 + 2w)
-      auto desc_slot = [&](uint32_t x) { return desc_s + (x % (kStages + 1)) * (4 * kSpikeBatch); };
+      // piece descriptor of spike k of round x (one lane writes it).  For the copy (read by a whole
+      // warp, one spike at a time): [0] 16-byte-aligned global addresses of the weight and meta
+      // pieces, [1].x weight chunks | meta chunks << 16.  For the fold (read by lane k of every
+      // warp, so stored spike-minor to keep the lanes on distinct banks): aux[k] = weight offset |
+      // meta offset << 8 | emission slot << 16, and the header's end[w][k].
+      auto desc_slot = [&](uint32_t x) { return desc_s + (x % (kStages + 1)) * (2 * kSpikeBatch); };
+      auto aux_slot = [&](uint32_t x) {
+        return reinterpret_cast<uint32_t*>(dsoa_s + (x % (kStages + 1)) * kSpikeBatch * (4 + 2 * kMaxWarps));
+      };
+      auto ends_slot = [&](uint32_t x) { return reinterpret_cast<uint16_t*>(aux_slot(x) + kSpikeBatch); };
       auto store_desc = [&](uint32_t x, uint32_t k) {
         const unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
         const uint4 h0 = *reinterpret_cast<const uint4*>(h), h1 = *reinterpret_cast<const uint4*>(h + 16);
@@ -733,11 +771,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         const uint32_t nm = len ? (mal + len * 2u + 15u) >> 4 : 0u;
         const unsigned long long gw = reinterpret_cast<unsigned long long>(a.rec_w) + (wbyte & ~15ull);
         const unsigned long long gm = reinterpret_cast<unsigned long long>(a.rec_meta) + (mbyte & ~15ull);
-        uint4* d = desc_slot(x) + 4 * k;
+        uint4* d = desc_slot(x) + 2 * k;
         d[0] = make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), (uint32_t)gm, (uint32_t)(gm >> 32));
-        d[1] = make_uint4(nw | (nm << 16), wal | (mal << 8) | ((uint32_t)((tm0 + ws) % D) << 16), 0u, 0u);
-        d[2] = make_uint4(h0.y, h0.z, h0.w, h1.x);
-        d[3] = make_uint4(h1.y, h1.z, h1.w, 0u);
+        d[1] = make_uint4(nw | (nm << 16), 0u, 0u, 0u);
+        aux_slot(x)[k] = wal | (mal << 8) | ((uint32_t)((tm0 + ws) % D) << 16);
+        uint16_t* en = ends_slot(x) + k;
+        const uint32_t hw[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+          en[(2 * q) * kSpikeBatch] = (uint16_t)(hw[q] & 0xffffu);
+          en[(2 * q + 1) * kSpikeBatch] = (uint16_t)(hw[q] >> 16);
+        }
       };
       // stage the records of round x: warp w copies spikes w, w + n_warps, ...; lane c copies the
       // 16-byte chunk c of the weight piece followed by the meta piece
@@ -747,8 +791,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         const uint32_t n = min(B, S_tot - x * B);
         unsigned char* sb = stage + (x % kStages) * (B * cap);
         for (uint32_t k = warp; k < n; k += n_warps) {
-          const uint4 d0 = ds[4 * k];
-          const uint32_t cnt = ds[4 * k + 1].x;
+          const uint4 d0 = ds[2 * k];
+          const uint32_t cnt = ds[2 * k + 1].x;
           const uint32_t nw = cnt & 0xffffu, nt2 = nw + (cnt >> 16);
           const unsigned char* gw = reinterpret_cast<const unsigned char*>(((unsigned long long)d0.y << 32) | d0.x);
           const unsigned char* gm = reinterpret_cast<const unsigned char*>(((unsigned long long)d0.w << 32) | d0.z);
@@ -808,15 +852,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
 
         // ---- fold round r: each warp, its target sub-range of every staged piece, in spike order
         {
-          const unsigned char* ds = reinterpret_cast<const unsigned char*>(desc_slot(r));
+          const uint32_t* aux_r = aux_slot(r);
+          const uint16_t* ends_r = ends_slot(r);
           const uint32_t n = min(B, S_tot - r * B);
           const uint32_t sbase = (r % kStages) * (B * cap);
           uint32_t len_k = 0, wb_k = 0, mb_k = 0, sb_k = 0;
           if ((uint32_t)lane < n) {
-            const unsigned char* dk = ds + 64u * lane;
-            const uint32_t e1 = *reinterpret_cast<const uint16_t*>(dk + 32 + 2 * warp);
-            const uint32_t e0 = warp ? *reinterpret_cast<const uint16_t*>(dk + 30 + 2 * warp) : 0u;
-            const uint32_t aux = *reinterpret_cast<const uint32_t*>(dk + 20);
+            const uint32_t e1 = ends_r[warp * kSpikeBatch + lane];
+            const uint32_t e0 = warp ? ends_r[(warp - 1) * kSpikeBatch + lane] : 0u;
+            const uint32_t aux = aux_r[lane];
             len_k = e1 - e0;
             const uint32_t pk = sbase + (uint32_t)lane * cap;
             wb_k = pk + (aux & 15u) + e0 * kWsz;
@@ -876,8 +920,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
             float wv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) fold_group<kRingSmem, 1>(ring, wtags, key + u, wv + u, lane, ring_red);
+            fold_four<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
           }
           for (; e < total; e += 32) {
             float wv;
