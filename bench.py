@@ -285,7 +285,8 @@ def our_arm(args):
                    "sim_steps_per_step": args.sim_steps, "dt_ms": spec.dt, "replicas": world,
                    "l2": "inputs larger than L2 (network %.1f GB)" % (st0["device_bytes"] / 1e9),
                    "blocks": st0["n_blocks"], "threads_per_block": st0["threads_per_block"],
-                   "ring_in_smem": st0["ring_in_smem"]},
+                   "ring_in_smem": st0["ring_in_smem"], "spikes_per_round": st0["spikes_per_round"],
+                   "smem_bytes": st0["smem_bytes"]},
         "rtf": rtf,
         "spikes": spikes, "events": events,
         "build_ms": st0["build_ms"],
@@ -354,6 +355,8 @@ def _form(cortex, W, name, args, stream, peak, peak_kind):
     out = {"workload": cfg["name"], "value": ev / (ms * 1e-3), "unit": UNIT, "rtf": (ms * 1e-3) / sim_s,
            "sim_steps": args.form_steps, "wall_value": ev / wall, "n_nets": st0["n_nets"],
            "neurons": st0["n_neurons"], "synapses": st0["n_synapses"], "build_ms": st0["build_ms"],
+           "blocks": st0["n_blocks"], "ring_in_smem": st0["ring_in_smem"], "spikes_per_round": st0["spikes_per_round"],
+           "smem_bytes": st0["smem_bytes"],
            "dtype": "bf16" if bpe == 5 else "f32",
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (persistent)",

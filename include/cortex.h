@@ -78,6 +78,7 @@ typedef struct cortex_options {
   int32_t use_graph;                 /* 0 = auto (on), 1 = on, -1 = off */
   int64_t raster_capacity;           /* 0 = auto; spikes kept on the device per network */
   double barrier_timeout_ms;         /* 0 = 2000 ms; device waits give up after this */
+  int32_t spikes_per_round;          /* 0 = auto (the largest that fits, at most 32); else 1..32 */
   int32_t balance;                   /* block plan of a batch: 0 = equal targets per block,
                                         1 = equal synapses per block (targets x in-degree) */
   int32_t test_withhold_block;       /* test hook, 0 = off.  b + 1: block b of the persistent
@@ -102,6 +103,8 @@ typedef struct cortex_stats_t {
   int32_t ring_in_smem;              /* 1 if the ring lives in shared memory */
   int32_t mode;                      /* CORTEX_MODE_* in use */
   int64_t device_bytes;              /* device memory held by the handle */
+  int32_t spikes_per_round;          /* spikes staged per delivery round */
+  int32_t smem_bytes;                /* dynamic shared memory per block of the step kernel */
 } cortex_stats_t;
 
 typedef struct cortex_net cortex_net;

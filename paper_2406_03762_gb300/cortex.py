@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
         ("ring", ctypes.c_int32), ("mode", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
         ("targets_per_block", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("raster_capacity", ctypes.c_int64), ("barrier_timeout_ms", ctypes.c_double),
-        ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
+        ("spikes_per_round", ctypes.c_int32), ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
     ]
 
 
@@ -53,6 +53,7 @@ class Stats(ctypes.Structure):
         ("build_ms", ctypes.c_double), ("simulate_ms", ctypes.c_double), ("simulate_steps", ctypes.c_int64),
         ("simulate_events", ctypes.c_int64), ("n_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
         ("ring_in_smem", ctypes.c_int32), ("mode", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+        ("spikes_per_round", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -344,15 +344,17 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   const size_t per_spike = (size_t)kStages * (h->cap_w + h->cap_m);  // staging bytes per spike of a round
   const size_t base = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, false, 0);
   const size_t ring_bytes = (size_t)h->max_depth * h->max_nt * 4;
-  auto batch_for = [&](size_t fixed) -> int {
-    if (fixed >= smem_cap) return 0;
-    return (int)std::min<size_t>(kSpikeBatch, (smem_cap - fixed) / per_spike);
+  // spikes per delivery round: the largest (up to kSpikeBatch) whose layout fits
+  auto batch_for = [&](bool ring) -> int {
+    for (int b = o.spikes_per_round > 0 ? o.spikes_per_round : kSpikeBatch; b >= 1; --b)
+      if (step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, ring, (int)(per_spike * b)) <= smem_cap) return b;
+    return 0;
   };
   bool smem_ring;
   if (o.ring == CORTEX_RING_SMEM) smem_ring = true;
   else if (o.ring == CORTEX_RING_GLOBAL) smem_ring = false;
-  else smem_ring = batch_for(base + ring_bytes) >= 16;
-  const int b = batch_for(base + (smem_ring ? ring_bytes : 0));
+  else smem_ring = batch_for(true) >= 16;
+  const int b = batch_for(smem_ring);
   if (b < 1)
     return fail(CORTEX_ERR_UNSUPPORTED, "shared memory too small for this plan (ring " + std::to_string(ring_bytes) +
                                             " B, state " + std::to_string(base) + " B, staging per spike " +
@@ -418,6 +420,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
   if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
   if (o.balance < 0 || o.balance > 1) return fail(CORTEX_ERR_ARG, "balance");
+  if (o.spikes_per_round < 0 || o.spikes_per_round > kSpikeBatch) return fail(CORTEX_ERR_ARG, "spikes_per_round must be 0..32");
 
   cortex_net* h = new (std::nothrow) cortex_net();
   if (!h) return fail(CORTEX_ERR_OOM, "handle");
@@ -766,6 +769,8 @@ int cortex_stats(cortex_net* h, cortex_stats_t* st) {
   st->ring_in_smem = h->ring_smem ? 1 : 0;
   st->mode = h->mode;
   st->device_bytes = (int64_t)h->device_bytes;
+  st->spikes_per_round = h->batch;
+  st->smem_bytes = (int32_t)h->smem;
   return CORTEX_OK;
 }
 

@@ -73,8 +73,6 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   o = align_to(o, 16);
   L.ids = o;
   o += kIdCap * 4;
-  L.mbl = o;   // mailbox lines read at the barrier: one per block of the network
-  o += (uint32_t)(max_nb * kMboxWords * 8);
   L.mbi = o;   // the block's first spike ids of the window (local, u16), for its mailbox line
   o += align_to(kInlMax * 2, 16);
   L.mbc = o;   // the block's spike count of every step of the window
@@ -92,6 +90,9 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   o = align_to(o, 16);
   L.tags = o;
   o += ring_smem ? align_to((uint32_t)(max_depth * max_nt), 16) : (uint32_t)(kMaxWarps * kTagHash);
+  o = align_to(o, 128);
+  L.mbl = o;   // mailbox lines read at the barrier: one per block of the network
+  o += (uint32_t)(max_nb * kMboxWords * 8);
   o = align_to(o, 128);
   L.stage = o;
   o += (uint32_t)stage_bytes;
