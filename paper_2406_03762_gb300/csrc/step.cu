@@ -690,7 +690,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
       }
       // spike ids of the window into shared memory (window order: step, then id); raster.  One
       // thread per (window step, block): the ids come from the block's mailbox line (persistent
-      // kernel, first ids of its window) or from its global list
+      // kernel, first ids of its window) or from its global list.  The same thread starts the
+      // header copy (32-byte header, 8-byte row start) of every spike of the first kStages rounds.
+      const uint32_t B0 = (uint32_t)a.batch;
       for (int e = tid; e < E; e += blockDim.x) {
         const uint32_t o = cnt_s[e], c = cnt_s[e + 1] - o;
         if (c == 0) continue;
@@ -709,6 +711,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
                                   ? (uint32_t)b * (uint32_t)tb_full + ((uint32_t)(ml[pw / 3u] >> (16u * (pw % 3u))) & 0xffffu)
                                   : __ldcg(src + q);
           if (o + q < (uint32_t)kIdCap) ids_s[o + q] = id;
+          if (o + q < (uint32_t)kStages * B0) {
+            const uint32_t x = (o + q) / B0, k = (o + q) - x * B0;
+            unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
+            const uint4* hp = a.hdr + 2 * (hdr_net + (int64_t)id * nb + wk.group);
+            cp_async16(h, hp);
+            cp_async16(h + 16, hp + 1);
+            cp_async8(h + 32, a.row_base + row_off + id);
+          }
           if (mine) {
             const unsigned long long pos = raster_total + o + q;
             if ((long long)pos < raster_cap) {
@@ -721,6 +731,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         }
       }
       raster_total += S_tot;
+      cp_async_commit();
+      cp_async_wait<0>();  // the header copies of the first kStages rounds
       __syncthreads();
 
       const uint32_t R = (S_tot + B - 1) / B;  // delivery rounds of this window
@@ -811,15 +823,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
       // r + kStages from headers fetched kHdrAhead - kStages iterations earlier (whose groups are
       // complete by then since kHdrAhead >= 2 kStages - 1); fold round r.
       if (R > 0) {
-        // headers of the first kStages rounds (waited for here), descriptors, then the headers of
-        // rounds kStages .. kHdrAhead - 1 and the records of the first kStages - 1 rounds
-        for (uint32_t i = tid; i < min(R, (uint32_t)kStages) * B; i += blockDim.x) {
-          const uint32_t x = i / B, k = i % B;
-          if (x * B + k < S_tot) fetch_hdr(x, k);
-        }
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
+        // descriptors of the first kStages rounds (their headers were copied with the ids), then the
+        // headers of rounds kStages .. kHdrAhead - 1 and the records of the first kStages - 1 rounds
         for (uint32_t i = tid; i < min(R, (uint32_t)kStages) * B; i += blockDim.x) {
           const uint32_t x = i / B, k = i % B;
           if (x * B + k < S_tot) store_desc(x, k);
