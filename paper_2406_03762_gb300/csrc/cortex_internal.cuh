@@ -10,14 +10,16 @@
 //   row_base  u64 per source: first record of the source's row, relative to the network's base.
 //   headers   one 32-byte header per (source, block), stored source-major: word 0 = first record of
 //             the block's piece relative to the row (low 16 bits) | flags (bit 16 + w: warp w's piece
-//             repeats a cell), then u16 end[w] for the block's delivery warps w = 0..13 (entries of
-//             warps 0..w; unused entries repeat the total).
+//             repeats a cell; informational), then u16 end[w] for the block's delivery warps
+//             w = 0..13 (entries of warps 0..w; unused entries repeat the total).
 //   state     V (f32), I (f32), refractory counter (i32) per neuron.
 //   ring      per block [D][T_b] floats, D = d_max + 1: cell (slot, j) holds the input due at the
 //             step t with t mod D == slot for local target j.
 //   pub       spike lists published per window: ids[(parity*W_max + ws) * n_total + pub_base + k],
-//             counts[(parity*W_max + ws) * n_blocks + block], mailbox[block] = (windows completed,
-//             count of the window's first step).
+//             counts[(parity*W_max + ws) * n_blocks + block] (read by split launches, and by the
+//             persistent kernel only beyond a mailbox line's capacity);
+//             mailbox[parity][block][16] u64 words = (window tag << 48) | payload;
+//             windows[block] = windows completed (kept across launches).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>

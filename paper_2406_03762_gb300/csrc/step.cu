@@ -22,10 +22,17 @@
 // them; the ring has D = d_max + 1 slots so that no delivery reaches the pending slot.  Launches
 // without the barrier (split mode) run whole steps, at most d_min per window.
 //
-// Delivery runs in rounds of up to kSpikeBatch spikes.  All warps stage the record segments of
-// round r + kStages - 1 into shared memory with 16-byte cp.async copies (each spike has a
-// fixed-size region of its slot), then fold round r; the headers of round r + kStages load into
-// registers meanwhile.  So kStages - 1 rounds of records are always in flight.
+// Publication and barrier: each block writes one 128-byte mailbox line per window whose 64-bit
+// words all carry the window's tag (step counts, then up to 45 spike ids), and bulk-prefetches
+// the rows of its spiking neurons into L2; reading every line of the network with the tag is the
+// barrier.  The next window's Poisson draws are made by the threads that do not poll.
+//
+// Delivery runs in rounds of up to kSpikeBatch spikes.  Headers (and row starts) are copied into
+// shared memory kHdrAhead rounds ahead; one lane per spike turns them into a piece descriptor
+// (global addresses and 16-byte chunk counts for the copy, spike-minor offsets and per-warp ends
+// for the fold); all warps stage the records of round r + kStages - 1 with 16-byte cp.async copies
+// (each spike has a fixed-size region of its slot), then fold round r.  So kStages - 1 rounds of
+// records are always in flight.
 #include <type_traits>
 
 #include "cortex_internal.cuh"
