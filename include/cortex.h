@@ -80,11 +80,15 @@ typedef struct cortex_options {
   double barrier_timeout_ms;         /* 0 = 2000 ms; device waits give up after this */
   int32_t spikes_per_round;          /* 0 = auto (the largest that fits, at most 32); else 1..32 */
   int32_t balance;                   /* block plan of a batch: 0 = equal targets per block,
-                                        1 = equal synapses per block (targets x in-degree) */
+                                        1 = equal synapses per block (targets x in-degree),
+                                        2 = equal work per block, with net_work[b] the cost of one
+                                        target of network b per step (needs net_work) */
   int32_t test_withhold_block;       /* test hook, 0 = off.  b + 1: block b of the persistent
                                         kernel never publishes its spikes, so every block's bounded
                                         wait at the window barrier runs out and cortex_simulate
                                         returns CORTEX_ERR_TIMEOUT (error path of the barrier) */
+  const float* net_work;             /* balance 2: n_nets finite costs > 0 (any common unit), read
+                                        by the build only; caller-owned; NULL otherwise */
 } cortex_options;
 
 typedef struct cortex_stats_t {
@@ -129,16 +133,22 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
 /* Autotuner (the paper has no counterpart: its partition is fixed by processes and threads).
  * Builds the network(s) of params / seeds with each candidate plan -- warps per block, i.e. the
  * number and width of the per-warp indegree sub-graphs (Sec. III-B), in {8, 10, 12, 14}, times the
- * block plan (base->balance 0 or 1) -- simulates trial_steps > 0 steps after one untimed launch,
- * frees it, and returns in *best the options of the fastest candidate (the other fields copied
- * from base, which may be NULL).  The simulation results do not depend on the plan (the
- * summation order is fixed by emission step, source and draw); only the time does.
+ * block plan -- simulates trial_steps > 0 steps after one untimed launch, frees it, and returns
+ * in *best the options of the fastest candidate (the other fields copied from base, which may be
+ * NULL).  Block plans: balance 0 and 1, and, when net_work_out is not NULL and n_nets > 1,
+ * balance 2 with each network's cost per target and step taken from the first candidate's
+ * trial: the synaptic events it delivered per target and step, plus a fixed cost of one target
+ * update (three values tried).  net_work_out: NULL or n_nets floats, caller-owned; when a
+ * balance-2 candidate wins, it receives that candidate's costs and best->net_work points to it,
+ * so it must outlive every build made with *best.  The simulation results do not depend on the
+ * plan (the summation order is fixed by emission step, source and draw); only the time does.
  * best_ms_per_step and n_tried (candidates that could be built) may be NULL.  Candidates that
  * exceed the layout limits are skipped.  Errors: CORTEX_ERR_ARG, CORTEX_ERR_UNSUPPORTED (no
  * candidate could be built), CORTEX_ERR_CUDA, CORTEX_ERR_TIMEOUT, CORTEX_ERR_OOM. */
 int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t n_nets,
                     const cortex_options* base, int32_t trial_steps, void* stream,
-                    cortex_options* best, double* best_ms_per_step, int32_t* n_tried);
+                    cortex_options* best, double* best_ms_per_step, int32_t* n_tried,
+                    float* net_work_out);
 
 /* Advance every network by n_steps >= 0 steps from the current step (Sec. II-B loop: deliver,
  * update, compact spikes).  Continuing in pieces gives the same result as one call.

@@ -43,7 +43,13 @@ class Options(ctypes.Structure):
         ("targets_per_block", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("raster_capacity", ctypes.c_int64), ("barrier_timeout_ms", ctypes.c_double),
         ("spikes_per_round", ctypes.c_int32), ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
+        ("net_work", ctypes.POINTER(ctypes.c_float)),
     ]
+
+    def work(self):
+        """The per-network costs of a balance-2 plan (list of floats), or None."""
+        keep = getattr(self, "_work", None)
+        return None if keep is None or not self.net_work else list(keep)
 
 
 class Stats(ctypes.Structure):
@@ -104,7 +110,7 @@ def load(build_if_missing: bool = False):
     L.cortex_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int64, P(ctypes.c_uint32)]
     L.cortex_subgraph_noalloc.argtypes = [P(Params), ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp]
     L.cortex_autotune.argtypes = [P(Params), P(ctypes.c_uint64), ctypes.c_int32, P(Options), ctypes.c_int32, vp,
-                                  P(Options), P(ctypes.c_double), P(ctypes.c_int32)]
+                                  P(Options), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_float)]
     for name in EXPORTED:
         if name not in ("cortex_free", "cortex_strerror", "cortex_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -137,10 +143,21 @@ def params_from_spec(spec) -> Params:
 
 
 def make_options(**kw) -> Options:
+    """Options with the given fields set; net_work takes a sequence of floats (kept alive by the
+    returned object)."""
     o = Options()
     for k, v in kw.items():
-        setattr(o, k, v)
+        if k == "net_work":
+            _set_work(o, v)
+        else:
+            setattr(o, k, v)
     return o
+
+
+def _set_work(o: Options, values):
+    arr = (ctypes.c_float * len(values))(*[float(x) for x in values])
+    o._work = arr
+    o.net_work = ctypes.cast(arr, ctypes.POINTER(ctypes.c_float))
 
 
 def _stream_handle(stream) -> int | None:
@@ -153,7 +170,8 @@ def _stream_handle(stream) -> int | None:
 
 def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000, stream=None):
     """cortex_autotune: the fastest plan (warps per block x block balance) for these networks.
-    Returns (Options, ms per simulation step, number of candidates built)."""
+    Returns (Options, ms per simulation step, number of candidates built); a balance-2 plan keeps
+    its per-network costs alive with the returned Options."""
     L = load()
     if not isinstance(specs, (list, tuple)):
         specs, seeds = [specs], [seeds]
@@ -162,9 +180,14 @@ def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000,
     best = Options()
     ms = ctypes.c_double(0.0)
     n = ctypes.c_int32(0)
+    work = (ctypes.c_float * len(specs))()
     rc = L.cortex_autotune(arr, sd, len(specs), ctypes.byref(base) if base is not None else None, int(trial_steps),
-                           _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms), ctypes.byref(n))
+                           _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms), ctypes.byref(n), work)
     _check(rc, "cortex_autotune")
+    if best.balance == 2:
+        best._work = work  # best.net_work points into it
+    else:
+        best.net_work = None
     return best, float(ms.value), int(n.value)
 
 

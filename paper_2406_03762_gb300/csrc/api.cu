@@ -4,6 +4,7 @@
 // delivery launches), and the data accessors.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -76,7 +77,7 @@ struct cortex_net {
   bool ring_smem = false;
   bool ring_red = false;  // global ring adds by the L2 reduction unit (exact for the weights)
   int mode = CORTEX_MODE_PERSISTENT;
-  int stage_bytes = 0, batch = 32, cap_w = 0, cap_m = 0;
+  int stage_bytes = 0, batch = 32;  // largest staging area, fewest spikes per round (stats)
   size_t smem = 0;
   int steps_per_launch = 1000;
   bool use_graph = true;
@@ -85,7 +86,8 @@ struct cortex_net {
   long long timeout_ns = 2000000000ll;
   int32_t withhold_block = -1;
   bool timed_out = false;  // a device wait gave up: the barrier epochs are inconsistent
-  uint32_t max_seg_len = 0;
+  std::vector<uint32_t> max_seg_len;  // longest (source, block) piece of each network
+  size_t smem_cap = 0;                 // dynamic shared memory a block may use
   // bookkeeping
   int64_t step = 0;
   int64_t spikes_cleared = 0;
@@ -135,32 +137,63 @@ int validate_params(const cortex_params& p, std::string& why) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// The most targets one block of network p may own: its shared-memory layout (ring in global
+// memory) must leave staging for two spikes per round, with the expected piece of a source
+// (t K / N records for uniformly drawn sources) plus six standard deviations.
+int64_t max_block_targets(const cortex_params& p, int wsz, int n_warps, size_t smem_cap) {
+  const int64_t n = (int64_t)p.n_exc + p.n_inh, k = std::max<int64_t>(1, (int64_t)p.k_exc + p.k_inh);
+  auto fits = [&](int64_t t) {
+    const double lam = (double)t * (double)k / (double)n;
+    int cw = 0, cm = 0;
+    step_staging_caps((int)std::ceil(lam + 6.0 * std::sqrt(lam) + 16.0), wsz, &cw, &cm);
+    const size_t fixed = step_smem_bytes((int)t, p.d_max + 1, p.d_min + 1, (int)ceil_div(n, t), false, 0);
+    return fixed + (size_t)2 * kStages * (cw + cm) <= smem_cap;
+  };
+  int64_t lo = std::min<int64_t>(n, 32ll * n_warps), hi = std::min<int64_t>(n, 65535);
+  if (fits(hi)) return hi;
+  while (hi - lo > 1) {  // fits(lo) is assumed: the smallest block always fits
+    const int64_t mid = (lo + hi) / 2;
+    (fits(mid) ? lo : hi) = mid;
+  }
+  return lo;
+}
+
 // Targets per block for every network so that all blocks are co-resident (one per SM).  Every
-// network is cut into equal blocks.  balance 0: one target budget T for all networks; balance 1:
-// one synapse budget for all networks (a network of in-degree K gets blocks of about budget / K
-// targets), so that blocks of a batch with uneven in-degrees carry similar delivery work.  The
-// budget grows until the blocks fit on the SMs.
+// network is cut into equal blocks.  A budget common to all networks sets the size of their
+// blocks: balance 0, targets (T per block); balance 1, synapses (a network of in-degree K gets
+// about budget / K targets per block), so that blocks of a batch with uneven in-degrees carry
+// similar delivery work; balance 2, work (a network whose targets cost w each per step gets about
+// budget / w), so that blocks of networks with uneven firing rates finish their steps together.
+// No block exceeds max_block_targets.  The budget grows until the blocks fit on the SMs.
 int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb) {
   const int cap = h->n_sm;  // one block per SM
   const int64_t tmin = 32ll * h->n_warps;
-  int64_t n_total = 0, syn_total = 0, kmax = 1;
-  for (auto& p : h->params) {
+  const int wsz = h->wdtype == CORTEX_BF16 ? 2 : 4;
+  const bool fixed_t = o.targets_per_block > 0;
+  const int mode = fixed_t ? 0 : o.balance;
+  std::vector<int64_t> tcap(h->n_nets);
+  std::vector<double> cost(h->n_nets);  // budget units per target of each network
+  int64_t n_total = 0;
+  double total = 0.0, cmax = 0.0;
+  for (int b = 0; b < h->n_nets; ++b) {
+    const cortex_params& p = h->params[b];
     const int64_t n = (int64_t)p.n_exc + p.n_inh, k = std::max<int64_t>(1, (int64_t)p.k_exc + p.k_inh);
+    tcap[b] = max_block_targets(p, wsz, h->n_warps, h->smem_cap);
+    cost[b] = mode == 0 ? 1.0 : mode == 1 ? (double)k : (double)o.net_work[b];
     n_total += n;
-    syn_total += n * k;
-    kmax = std::max(kmax, k);
+    total += (double)n * cost[b];
+    cmax = std::max(cmax, cost[b]);
   }
-  const bool by_syn = o.balance == 1 && o.targets_per_block <= 0;
-  int64_t T = std::max<int64_t>(tmin, ceil_div(n_total, cap));
-  int64_t S = std::max<int64_t>(tmin * kmax, ceil_div(syn_total, cap));  // synapse budget (balance 1)
-  if (o.targets_per_block > 0) T = std::min<int64_t>(T, o.targets_per_block);
+  double S = mode == 0 ? (double)std::max<int64_t>(tmin, ceil_div(n_total, cap))
+                       : std::max((double)tmin * cmax, std::ceil(total / cap));
+  if (fixed_t) S = std::min<double>(S, o.targets_per_block);
   for (int iter = 0; iter < 10000; ++iter) {
     int64_t blocks = 0;
     tb.assign(h->n_nets, 0);
     for (int b = 0; b < h->n_nets; ++b) {
       const int64_t n = (int64_t)h->params[b].n_exc + h->params[b].n_inh;
-      const int64_t k = std::max<int64_t>(1, (int64_t)h->params[b].k_exc + h->params[b].k_inh);
-      int64_t t = by_syn ? std::min<int64_t>(n, std::max<int64_t>(tmin, S / k)) : std::min<int64_t>(n, T);
+      int64_t t = std::min<int64_t>(n, std::max<int64_t>(tmin, (int64_t)(S / cost[b])));
+      if (!fixed_t) t = std::min(t, tcap[b]);
       // balance the blocks of one network
       const int64_t nb = ceil_div(n, t);
       t = ceil_div(n, nb);
@@ -170,9 +203,8 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
     bool ok = true;
     for (int b = 0; b < h->n_nets; ++b) ok = ok && tb[b] <= 65535;
     if (!ok) return fail(CORTEX_ERR_UNSUPPORTED, "targets per block above 65535 (network too large for one GPU plan)");
-    if (blocks <= cap || o.targets_per_block > 0) return CORTEX_OK;
-    T = T + std::max<int64_t>(1, T / 16);
-    S = S + std::max<int64_t>(1, S / 16);
+    if (blocks <= cap || fixed_t) return CORTEX_OK;
+    S += std::max(1.0, std::floor(S / 16));
   }
   return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
 }
@@ -217,13 +249,6 @@ StepArgs make_args(cortex_net* h) {
   a.events = h->events;
   a.err = h->err;
   a.step_counter = h->step_counter;
-  a.stage_bytes = h->stage_bytes;
-  a.batch = h->batch;
-  a.cap_w = h->cap_w;
-  a.cap_m = h->cap_m;
-  a.max_nt = h->max_nt;
-  a.max_depth = h->max_depth;
-  a.max_nb = h->max_nb;
   a.timeout_ns = h->timeout_ns;
   a.ring_red = h->ring_red ? 1 : 0;
   a.bf16 = h->wdtype == CORTEX_BF16 ? 1 : 0;
@@ -324,7 +349,7 @@ int build_network(cortex_net* h, int b, const std::vector<int32_t>& tb) {
     if (e == cudaSuccess) e = launch_build_fill_net(h->nets_d, b, (int32_t)n, g0, ng, tb[b], cursor, keys, st);
     if (e == cudaSuccess)
       e = launch_build_finalize_net(h->nets_d, h->work_d, b, g0, ng, h->n_warps, cnt, cursor, keys, off_all,
-                                    h->row_base, h->rec_w, h->rec_meta, h->hdr, h->err, h->max_seg, st);
+                                    h->row_base, h->rec_w, h->rec_meta, h->hdr, h->err, h->max_seg + b, st);
     if (e != cudaSuccess) rc = fail(CORTEX_ERR_CUDA, std::string("builder: ") + cudaGetErrorString(e));
   }
   cudaFreeAsync(cnt_all, st);
@@ -335,30 +360,38 @@ int build_network(cortex_net* h, int b, const std::vector<int32_t>& tb) {
   return rc;
 }
 
+// Shared-memory layout of each network: state for its blocks' targets, and staging bytes per
+// spike from its own longest piece.  Each network's rounds hold as many spikes (up to 32) as fit
+// next to its state; the launch reserves the largest layout.  The ring goes to shared memory when
+// every network still gets rounds of at least 16 spikes next to it.
 int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
-  cudaDeviceProp prop;
-  CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
-  const size_t smem_cap = (size_t)prop.sharedMemPerBlockOptin - 1024;  // room for static shared memory
   const int wsz = h->wdtype == CORTEX_BF16 ? 2 : 4;
-  step_staging_caps((int)std::max<uint32_t>(h->max_seg_len, 1u), wsz, &h->cap_w, &h->cap_m);
-  const size_t per_spike = (size_t)kStages * (h->cap_w + h->cap_m);  // staging bytes per spike of a round
-  const size_t base = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, false, 0);
-  const size_t ring_bytes = (size_t)h->max_depth * h->max_nt * 4;
-  // spikes per delivery round: the largest (up to kSpikeBatch) whose layout fits
-  auto batch_for = [&](bool ring) -> int {
-    for (int b = o.spikes_per_round > 0 ? o.spikes_per_round : kSpikeBatch; b >= 1; --b)
-      if (step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, ring, (int)(per_spike * b)) <= smem_cap) return b;
-    return 0;
+  const int cap_round = o.spikes_per_round > 0 ? o.spikes_per_round : kSpikeBatch;
+  const int nn = h->n_nets;
+  std::vector<int> cw(nn), cm(nn);
+  std::vector<size_t> per(nn);  // staging bytes per spike of a round (kStages rounds in flight)
+  auto layout = [&](int b, bool ring, size_t stage) {
+    const NetDev& d = h->nets_h[b];
+    return step_smem_bytes(h->work_h[d.first_block].nt, d.depth, d.window, d.n_blocks, ring, (int)stage);
   };
+  auto room = [&](int b, bool ring) -> size_t {  // staging bytes that fit next to the rest
+    const size_t fixed = layout(b, ring, 0);
+    return fixed >= h->smem_cap ? 0 : (h->smem_cap - fixed) / 16 * 16;
+  };
+  size_t fit_smem = SIZE_MAX, fit_glob = SIZE_MAX;  // fewest spikes per round over the networks
+  for (int b = 0; b < nn; ++b) {
+    step_staging_caps((int)std::max<uint32_t>(h->max_seg_len[b], 1u), wsz, &cw[b], &cm[b]);
+    per[b] = (size_t)kStages * (cw[b] + cm[b]);
+    fit_smem = std::min(fit_smem, room(b, true) / per[b]);
+    fit_glob = std::min(fit_glob, room(b, false) / per[b]);
+  }
   bool smem_ring;
   if (o.ring == CORTEX_RING_SMEM) smem_ring = true;
   else if (o.ring == CORTEX_RING_GLOBAL) smem_ring = false;
-  else smem_ring = batch_for(true) >= 16;
-  const int b = batch_for(smem_ring);
-  if (b < 1)
-    return fail(CORTEX_ERR_UNSUPPORTED, "shared memory too small for this plan (ring " + std::to_string(ring_bytes) +
-                                            " B, state " + std::to_string(base) + " B, staging per spike " +
-                                            std::to_string(per_spike) + " B)");
+  else smem_ring = fit_smem >= 16;
+  if ((smem_ring ? fit_smem : fit_glob) < 1)
+    return fail(CORTEX_ERR_UNSUPPORTED, std::string("shared memory too small for this plan (ring in ") +
+                                            (smem_ring ? "shared" : "global") + " memory)");
   h->ring_smem = smem_ring;
   {
     // reductions flush subnormals: allowed when every weight is 0 or >= 2^-102 in magnitude (with
@@ -369,9 +402,21 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
         ok = ok && (w == 0.0f || std::fabs(w) >= std::ldexp(1.0f, -102));
     h->ring_red = ok && !smem_ring;
   }
-  h->batch = b;
-  h->stage_bytes = (int)(per_spike * b);
-  h->smem = step_smem_bytes(h->max_nt, h->max_depth, h->w_max, h->max_nb, smem_ring, h->stage_bytes);
+  h->smem = 0;
+  h->stage_bytes = 0;
+  h->batch = kSpikeBatch;
+  for (int b = 0; b < nn; ++b) {
+    const int bb = (int)std::min<size_t>((size_t)cap_round, room(b, smem_ring) / per[b]);
+    NetDev& d = h->nets_h[b];
+    d.batch = bb;
+    d.cap_w = cw[b];
+    d.cap_m = cm[b];
+    d.stage_bytes = (int32_t)(per[b] * bb);
+    h->smem = std::max(h->smem, layout(b, smem_ring, (size_t)d.stage_bytes));
+    h->stage_bytes = std::max(h->stage_bytes, d.stage_bytes);
+    h->batch = std::min(h->batch, bb);
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * nn, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(step_kernel_attributes(h->smem));
   return CORTEX_OK;
 }
@@ -419,7 +464,12 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..14");
   if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
   if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
-  if (o.balance < 0 || o.balance > 1) return fail(CORTEX_ERR_ARG, "balance");
+  if (o.balance < 0 || o.balance > 2) return fail(CORTEX_ERR_ARG, "balance");
+  if (o.balance == 2) {
+    if (!o.net_work) return fail(CORTEX_ERR_ARG, "balance 2 needs net_work");
+    for (int b = 0; b < n_nets; ++b)
+      if (!(o.net_work[b] > 0.0f) || !std::isfinite(o.net_work[b])) return fail(CORTEX_ERR_ARG, "net_work must be finite and > 0");
+  }
   if (o.spikes_per_round < 0 || o.spikes_per_round > kSpikeBatch) return fail(CORTEX_ERR_ARG, "spikes_per_round must be 0..32");
 
   cortex_net* h = new (std::nothrow) cortex_net();
@@ -434,6 +484,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(fail(CORTEX_ERR_CUDA, "device properties"));
   if (prop.major < 10) return bail(fail(CORTEX_ERR_UNSUPPORTED, "needs a Blackwell GPU (sm_103a build)"));
   h->n_sm = prop.multiProcessorCount;
+  h->smem_cap = (size_t)prop.sharedMemPerBlockOptin - 1024;  // room for static shared memory
   h->n_nets = n_nets;
   h->params.assign(params, params + n_nets);
   h->seeds.assign(seeds, seeds + n_nets);
@@ -568,13 +619,13 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(h->alloc(&h->events, 8 * (size_t)n_nets), "alloc counters");
   TRY(h->alloc(&h->err, 16), "alloc err");
   TRY(h->alloc(&h->step_counter, 16), "alloc step");
-  TRY(h->alloc(&h->max_seg, 16), "alloc max_seg");
+  TRY(h->alloc(&h->max_seg, 4 * (size_t)n_nets), "alloc max_seg");
 
   TRY(cudaEventRecord(h->ev0, s), "event");
   TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * n_nets, cudaMemcpyHostToDevice, s), "upload nets");
   TRY(cudaMemcpyAsync(h->work_d, h->work_h.data(), sizeof(BlockWork) * h->n_blocks, cudaMemcpyHostToDevice, s), "upload work");
   TRY(cudaMemsetAsync(h->err, 0, 16, s), "memset");
-  TRY(cudaMemsetAsync(h->max_seg, 0, 16, s), "memset");
+  TRY(cudaMemsetAsync(h->max_seg, 0, 4 * (size_t)n_nets, s), "memset");
   TRY(cudaMemsetAsync(h->step_counter, 0, 16, s), "memset");
   TRY(launch_props(h->nets_d, n_nets, s), "propagators");
   TRY(cudaMemcpyAsync(h->nets_h.data(), h->nets_d, sizeof(NetDev) * n_nets, cudaMemcpyDeviceToHost, s), "download nets");
@@ -593,7 +644,8 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(cudaMemsetAsync(h->pub_cnt, 0, 4 * (size_t)2 * h->w_max * h->n_blocks, s), "memset counts");
   TRY(cudaMemsetAsync(h->raster_count, 0, 8 * (size_t)n_nets, s), "memset");
   TRY(cudaMemsetAsync(h->events, 0, 8 * (size_t)n_nets, s), "memset");
-  TRY(cudaMemcpyAsync(&h->max_seg_len, h->max_seg, 4, cudaMemcpyDeviceToHost, s), "download");
+  h->max_seg_len.assign(n_nets, 0u);
+  TRY(cudaMemcpyAsync(h->max_seg_len.data(), h->max_seg, 4 * (size_t)n_nets, cudaMemcpyDeviceToHost, s), "download");
   TRY(cudaEventRecord(h->ev1, s), "event");
   rc = check_err(h, "build");
   if (rc != CORTEX_OK) return bail(rc);
@@ -625,42 +677,74 @@ int cortex_build(const cortex_params* params, uint64_t seed, const cortex_option
 
 int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t n_nets, const cortex_options* base,
                     int32_t trial_steps, void* stream, cortex_options* best, double* best_ms_per_step,
-                    int32_t* n_tried) {
+                    int32_t* n_tried, float* net_work_out) {
   if (!params || !seeds || n_nets <= 0 || trial_steps <= 0 || !best) return fail(CORTEX_ERR_ARG, "cortex_autotune: arguments");
   cortex_options b0;
   memset(&b0, 0, sizeof(b0));
   if (base) b0 = *base;
-  // candidates: warps per block (the width of the per-warp sub-graphs) x block plan
+  // candidates: warps per block (the width of the per-warp sub-graphs) x block plan; the plans of
+  // balance 2 charge a target of network b its measured events per step plus a fixed update cost
+  struct Cand {
+    int balance, warps;
+    float update_cost;
+  };
   const int warps[] = {8, 10, 12, 14};
+  std::vector<Cand> cands;
+  for (int bal = 0; bal <= 1; ++bal)
+    for (int w : warps) cands.push_back({bal, w, 0.0f});
+  if (net_work_out && n_nets > 1)
+    for (float cu : {0.5f, 2.0f, 8.0f})
+      for (int w : warps) cands.push_back({2, w, cu});
+  std::vector<double> events_per_target;  // per network, from the first candidate that ran
+  std::vector<float> work(n_nets), best_work;
   double best_ms = -1.0;
   int tried = 0, last_rc = CORTEX_ERR_UNSUPPORTED;
-  for (int bal = 0; bal <= 1; ++bal)
-    for (int w : warps) {
-      cortex_options o = b0;
-      o.warps_per_block = w;
-      o.balance = bal;
-      cortex_net* h = nullptr;
-      int rc = cortex_build_batch(params, seeds, n_nets, &o, stream, &h);
-      if (rc == CORTEX_OK) rc = cortex_simulate(h, std::min<int64_t>(trial_steps, h->steps_per_launch));  // warm-up
-      double ms = 0.0;
-      if (rc == CORTEX_OK) {
-        rc = cortex_simulate(h, trial_steps);
-        ms = h->sim_ms;
-      }
-      if (h) cortex_free(h);
-      if (rc == CORTEX_ERR_CUDA || rc == CORTEX_ERR_TIMEOUT) return rc;  // not a property of the plan
-      if (rc != CORTEX_OK) {
-        last_rc = rc;
-        continue;
-      }
-      ++tried;
-      if (best_ms < 0.0 || ms < best_ms) {
-        best_ms = ms;
-        *best = o;
-      }
+  for (const Cand& c : cands) {
+    cortex_options o = b0;
+    o.warps_per_block = c.warps;
+    o.balance = c.balance;
+    o.net_work = nullptr;
+    if (c.balance == 2) {
+      if (events_per_target.empty()) continue;
+      for (int b = 0; b < n_nets; ++b) work[b] = (float)events_per_target[b] + c.update_cost;
+      o.net_work = work.data();
     }
+    cortex_net* h = nullptr;
+    int rc = cortex_build_batch(params, seeds, n_nets, &o, stream, &h);
+    if (rc == CORTEX_OK) rc = cortex_simulate(h, std::min<int64_t>(trial_steps, h->steps_per_launch));  // warm-up
+    double ms = 0.0;
+    if (rc == CORTEX_OK) {
+      rc = cortex_simulate(h, trial_steps);
+      ms = h->sim_ms;
+    }
+    if (rc == CORTEX_OK && events_per_target.empty()) {
+      std::vector<unsigned long long> e(n_nets);
+      if (cudaMemcpyAsync(e.data(), h->events, 8 * (size_t)n_nets, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        rc = CORTEX_ERR_CUDA;
+      events_per_target.resize(n_nets);
+      for (int b = 0; b < n_nets; ++b)
+        events_per_target[b] = (double)e[b] / ((double)h->nets_h[b].n * (double)std::max<int64_t>(h->step, 1));
+    }
+    if (h) cortex_free(h);
+    if (rc == CORTEX_ERR_CUDA || rc == CORTEX_ERR_TIMEOUT) return rc;  // not a property of the plan
+    if (rc != CORTEX_OK) {
+      last_rc = rc;
+      continue;
+    }
+    ++tried;
+    if (best_ms < 0.0 || ms < best_ms) {
+      best_ms = ms;
+      *best = o;
+      best_work = c.balance == 2 ? work : std::vector<float>();
+    }
+  }
   if (n_tried) *n_tried = tried;
   if (best_ms < 0.0) return fail(last_rc, "cortex_autotune: no candidate plan could be built");
+  if (best->balance == 2) {
+    std::copy(best_work.begin(), best_work.end(), net_work_out);
+    best->net_work = net_work_out;
+  }
   if (best_ms_per_step) *best_ms_per_step = best_ms / trial_steps;
   return CORTEX_OK;
 }

@@ -58,6 +58,8 @@ struct NetDev {
   float p11, p21, p22m1;                       // FP32 propagators (from FP64 on the device); P22 - 1
   float v_th, v_reset, j_ext;
   float w_exc, w_inh;                          // stored weights (bf16-rounded when wdtype = 1)
+  int32_t batch, cap_w, cap_m;                 // spikes per delivery round, staging bytes per spike
+  int32_t stage_bytes;                         // staging area of a block (shared-memory layout)
   // host-provided inputs for the propagator kernel
   float tau_m, c_m, tau_syn, t_ref, dt, nu_ext_hz, j_exc_in, j_inh_in;
   int64_t neuron_base;                         // offset of this network in V / I / R
@@ -110,10 +112,6 @@ struct StepArgs {
   int32_t ring_smem;                  // 1: ring slice in shared memory
   int32_t bf16;                       // 1: weights stored as bf16 (all networks of a handle)
   int32_t ring_red;                   // 1: adds into a global ring use the L2 reduction unit
-  int32_t stage_bytes;                // shared staging capacity for record segments
-  int32_t batch;                      // spikes per delivery round
-  int32_t cap_w, cap_m;               // staging bytes per spike: weight stream, meta stream
-  int32_t max_nt, max_depth, max_nb;  // shared-memory layout maxima over the blocks
   long long timeout_ns;
   int32_t withhold_block;             // test hook: this block never publishes (-1: none)
   // delivery-only launches (cortex_deliver): fixed emission step
@@ -287,7 +285,9 @@ cudaError_t launch_init_state(const NetDev* net_host, const NetDev* net_dev, int
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, cudaStream_t s);
 cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s);
 cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s);
-size_t step_smem_bytes(int max_nt, int max_depth, int w_max, int max_nb, bool ring_smem, int stage_bytes);
+// dynamic shared memory of a block of a network: nt targets per block (its largest block),
+// ring depth, window steps, nb blocks, staging bytes
+size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes);
 void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m);
 cudaError_t step_kernel_attributes(size_t smem);
 int step_occupancy(int threads, size_t smem, bool ring_smem);

@@ -50,42 +50,42 @@ __host__ __device__ inline uint32_t align_to(uint32_t x, uint32_t a) { return (x
 // ring updates, in separate tables, measured slower with reductions into a global ring.)
 constexpr int kTagHash = 2048;
 
-__host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int w_max, int max_nb, bool ring_smem,
+__host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window, int nb, bool ring_smem,
                                                   int stage_bytes) {
   SmemLayout L;
   uint32_t o = 0;
   L.ring = o;
-  o += ring_smem ? (uint32_t)(max_depth * max_nt * 4) : 0u;
+  o += ring_smem ? (uint32_t)(depth * nt * 4) : 0u;
   o = align_to(o, 16);
   L.sv = o;
-  o += max_nt * 4;
+  o += nt * 4;
   L.si = o;
-  o += max_nt * 4;
+  o += nt * 4;
   L.sr = o;    // refractory counters (32 bit; 16 bit when the ring is global, to leave room for staging)
-  o += max_nt * (ring_smem ? 4 : 2);
+  o += nt * (ring_smem ? 4 : 2);
   o = align_to(o, 16);
   L.thr = o;
   o += kPoissonCap * 4;
   L.cnt = o;
-  o += (uint32_t)(w_max * (max_nb + 1) * 4);
+  o += (uint32_t)(window * (nb + 1) * 4);
   o = align_to(o, 16);
   L.woffs = o;
-  o += (uint32_t)((w_max + 1) * 4);
+  o += (uint32_t)((window + 1) * 4);
   o = align_to(o, 16);
   L.wcnt = o;
   o += (kMaxWarps + 2) * 4;
   o = align_to(o, 16);
   L.wlist = o;  // per-warp spike lists of a step (local ids; 32 bit, 16 bit when the ring is global)
-  o += max_nt * (ring_smem ? 4 : 2);
+  o += nt * (ring_smem ? 4 : 2);
   o = align_to(o, 16);
   L.ids = o;
   o += kIdCap * 4;
   L.mbi = o;   // the block's first spike ids of the window (local, u16), for its mailbox line
   o += align_to(kInlMax * 2, 16);
   L.mbc = o;   // the block's spike count of every step of the window
-  o += align_to((uint32_t)(w_max * 4), 16);
+  o += align_to((uint32_t)(window * 4), 16);
   L.pk = o;    // Poisson counts of the window's I halves, [step][target] (persistent kernel)
-  o += align_to((uint32_t)(w_max * max_nt), 16);
+  o += align_to((uint32_t)(window * nt), 16);
   L.hdr = o;   // fetched headers: kHdrSlots rounds of (32-byte header, 8-byte row start, pad) per spike
   o += kHdrSlots * kSpikeBatch * 48;
   L.desc = o;  // piece descriptors, kStages + 1 rounds: 32 bytes per spike (copy), then per round
@@ -96,10 +96,10 @@ __host__ __device__ inline SmemLayout make_layout(int max_nt, int max_depth, int
   o += kMaxWarps * 32;
   o = align_to(o, 16);
   L.tags = o;
-  o += ring_smem ? align_to((uint32_t)(max_depth * max_nt), 16) : (uint32_t)(kMaxWarps * kTagHash);
+  o += ring_smem ? align_to((uint32_t)(depth * nt), 16) : (uint32_t)(kMaxWarps * kTagHash);
   o = align_to(o, 128);
   L.mbl = o;   // mailbox lines read at the barrier: one per block of the network
-  o += (uint32_t)(max_nb * kMboxWords * 8);
+  o += (uint32_t)(nb * kMboxWords * 8);
   o = align_to(o, 128);
   L.stage = o;
   o += (uint32_t)stage_bytes;
@@ -315,9 +315,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   const bool ring_red = a.ring_red != 0;
   const bool do_update = (a.phases & kPhaseUpdate) != 0;
   const bool do_deliver = (a.phases & kPhaseDeliver) != 0;
-  const uint32_t B = (uint32_t)a.batch, cap_w = (uint32_t)a.cap_w, cap = (uint32_t)(a.cap_w + a.cap_m);
+  // round size and staging bytes per spike of this block's network (its longest piece sets them)
+  const uint32_t B = (uint32_t)ndg.batch, cap_w = (uint32_t)ndg.cap_w, cap = (uint32_t)(ndg.cap_w + ndg.cap_m);
 
-  const SmemLayout L = make_layout(a.max_nt, a.max_depth, a.w_max, a.max_nb, kRingSmem, a.stage_bytes);
+  // the network's own layout (its blocks' targets, depth, window and block count)
+  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes);
   float* ring_s = reinterpret_cast<float*>(smem + L.ring);
   float* sV = reinterpret_cast<float*>(smem + L.sv);
   float* sI = reinterpret_cast<float*>(smem + L.si);
@@ -699,7 +701,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
       // thread per (window step, block): the ids come from the block's mailbox line (persistent
       // kernel, first ids of its window) or from its global list.  The same thread starts the
       // header copy (32-byte header, 8-byte row start) of every spike of the first kStages rounds.
-      const uint32_t B0 = (uint32_t)a.batch;
+      const uint32_t B0 = B;
       for (int e = tid; e < E; e += blockDim.x) {
         const uint32_t o = cnt_s[e], c = cnt_s[e + 1] - o;
         if (c == 0) continue;
@@ -1018,8 +1020,8 @@ cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStre
   return cudaGetLastError();
 }
 
-size_t step_smem_bytes(int max_nt, int max_depth, int w_max, int max_nb, bool ring_smem, int stage_bytes) {
-  return make_layout(max_nt, max_depth, w_max, max_nb, ring_smem, stage_bytes).total;
+size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes) {
+  return make_layout(nt, depth, window, nb, ring_smem, stage_bytes).total;
 }
 
 // staging bytes per spike: a segment of up to max_seg_len records, widened to 16-byte boundaries

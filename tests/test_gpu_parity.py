@@ -191,15 +191,22 @@ def test_deliver_counts_out_degree(cortex):
 
 
 def test_autotune_plan_does_not_change_results(cortex):
-    """The autotuner times candidate plans (warps per block x block balance).  Every plan gives the
-    same rasters, because the summation order does not depend on the partition, and the oracle's."""
+    """The autotuner times candidate plans (warps per block x block balance, including plans
+    balanced by the measured work of each network).  Every plan gives the same rasters, because
+    the summation order does not depend on the partition, and the oracle's.  A work-balanced plan
+    with uneven costs cuts the costly networks into several blocks."""
     specs, seeds = W.small_batch_specs()
     best, ms, n = cortex.autotune(specs, seeds, trial_steps=200)
-    assert n >= 2 and ms > 0
-    assert best.warps_per_block in (8, 10, 12, 14) and best.balance in (0, 1)
+    assert n >= 20 and ms > 0
+    assert best.warps_per_block in (8, 10, 12, 14) and best.balance in (0, 1, 2)
+    if best.balance == 2:
+        assert len(best.work()) == len(specs) and min(best.work()) > 0
+    uneven = cortex.make_options(warps_per_block=10, balance=2, net_work=[20.0, 1.0, 0.5, 3.0, 1.0, 8.0])
     rasters = []
-    for opts in (best, cortex.make_options(warps_per_block=8, balance=1), cortex.make_options()):
+    for opts in (best, cortex.make_options(warps_per_block=8, balance=1), uneven, cortex.make_options()):
         with cortex.Network(specs, seeds, opts) as net:
+            if opts is uneven:
+                assert net.stats()["n_blocks"] > len(specs)
             net.simulate(600)
             rasters.append([net.spikes(b) for b in range(len(specs))])
     for r in rasters[1:]:
