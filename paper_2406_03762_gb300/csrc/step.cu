@@ -537,8 +537,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         // Publication: the block's mailbox line for this window.  Every 64-bit word carries the
         // window's tag in its top 16 bits, so a reader that sees the tag in a word sees that word's
         // payload: count words (three u16 step counts each), then id words (three u16 local ids
-        // each).  The count words are release stores: they order the global id lists
-        // (read by others only beyond the line's capacity) before them.
+        // each).  When the window's spikes overflow the line, the count words are release
+        // stores: they order the global id lists (read by others only beyond the line's capacity)
+        // before them.  Otherwise a reader needs nothing but the line, and every word is a
+        // relaxed store (a release costs the block a fence on the barrier's critical path).  A
+        // reader accepts a word only with the tag it waits for, and the line is rewritten (two
+        // windows later) only after every block of the network has published the next window's
+        // line, which a block does after its polls of this line have returned.
         const unsigned long long tag = (unsigned long long)(((epoch + 1u) & 0x7fffu) | 0x8000u) << 48;
         const uint32_t nin = min(win_total, inl);
         if (tid < kMboxWords && blk != a.withhold_block) {
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
             }
           }
           unsigned long long* dst = a.mbox + ((size_t)par * a.n_blocks + blk) * kMboxWords + tid;
-          if (tid < n_cw) st_release_u64(dst, tag | pay);  // after the block's global id lists
+          if (tid < n_cw && win_total > inl) st_release_u64(dst, tag | pay);  // after the global id lists
           else st_relaxed_u64(dst, tag | pay);
         }
         // L2 prefetch of the spiking rows (every block of the network reads them after the
