@@ -183,6 +183,28 @@ int cortex_export_synapses(cortex_net* net, int32_t net_idx, int32_t t_begin, in
  * synaptic current (pA), remaining refractory steps.  Any pointer may be NULL. */
 int cortex_get_state(cortex_net* net, int32_t net_idx, float* v, float* i_syn, int32_t* refr);
 
+/* Ring of future synaptic input of network net_idx (the delay buffer of Sec. III-B): D = d_max
+ * + 1 slots per neuron, slot-major host array of D * n floats.  ring[s * n + i] is the summed
+ * input neuron i takes in at the one step t' in [t, t + D) with t' mod D == s, t being the
+ * current step (the next one cortex_simulate runs). */
+int cortex_get_ring(cortex_net* net, int32_t net_idx, float* ring);
+
+/* Checkpoint restore for network net_idx: V, I, refractory counts (each in 0..n_ref) and the ring
+ * (layout as cortex_get_ring), host arrays of its n neurons.  Any pointer may be NULL to leave
+ * that part unchanged.  Everything else a step reads is fixed by (params, seed, step): the
+ * connectivity and the counter-based Poisson drive.  So a handle built from the same params and
+ * seeds, given the state of every network and the step (cortex_set_step), continues a
+ * checkpointed simulation bit for bit (Sec. II-B loop).  The recorded raster and the counters
+ * are not part of the state.  Errors: CORTEX_ERR_ARG (index, or a refractory count outside
+ * 0..n_ref; nothing is changed), CORTEX_ERR_TIMEOUT (an earlier device wait of the handle timed
+ * out), CORTEX_ERR_CUDA. */
+int cortex_set_state(cortex_net* net, int32_t net_idx, const float* v, const float* i_syn,
+                     const int32_t* refr, const float* ring);
+
+/* Set the current step of every network of the handle (the first step the next cortex_simulate
+ * runs), step >= 0.  Errors: CORTEX_ERR_ARG, CORTEX_ERR_TIMEOUT, CORTEX_ERR_CUDA. */
+int cortex_set_step(cortex_net* net, int64_t step);
+
 /* The FP32 constants network net_idx uses, as computed on the device: out6 = {P11, P21,
  * P22 - 1 (= expm1(-h/tau_m), the form the update uses), w_exc, w_inh, j_ext}; thr = Poisson thresholds (up to 64 words), *n_thr their count,
  * *n_ref the refractory steps. */

@@ -70,7 +70,7 @@ EXPORTED = [
     "cortex_build", "cortex_build_batch", "cortex_simulate", "cortex_spikes", "cortex_clear_spikes",
     "cortex_stats", "cortex_export_synapses", "cortex_get_state", "cortex_constants", "cortex_deliver",
     "cortex_philox", "cortex_free", "cortex_strerror", "cortex_last_error", "cortex_subgraph_noalloc",
-    "cortex_autotune",
+    "cortex_autotune", "cortex_get_ring", "cortex_set_state", "cortex_set_step",
 ]
 
 _lib = None
@@ -109,6 +109,10 @@ def load(build_if_missing: bool = False):
                                  ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_int64)]
     L.cortex_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_int64, P(ctypes.c_uint32)]
     L.cortex_subgraph_noalloc.argtypes = [P(Params), ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp]
+    L.cortex_get_ring.argtypes = [vp, ctypes.c_int32, P(ctypes.c_float)]
+    L.cortex_set_state.argtypes = [vp, ctypes.c_int32, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_int32),
+                                   P(ctypes.c_float)]
+    L.cortex_set_step.argtypes = [vp, ctypes.c_int64]
     L.cortex_autotune.argtypes = [P(Params), P(ctypes.c_uint64), ctypes.c_int32, P(Options), ctypes.c_int32, vp,
                                   P(Options), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_float)]
     for name in EXPORTED:
@@ -130,8 +134,8 @@ def _check(rc: int, where: str):
         raise CortexError(rc, where, f"{L.cortex_strerror(rc).decode()}: {L.cortex_last_error().decode()}")
 
 
-def _p(a: np.ndarray, ct):
-    return a.ctypes.data_as(ctypes.POINTER(ct))
+def _p(a: np.ndarray | None, ct):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
 
 
 def params_from_spec(spec) -> Params:
@@ -260,6 +264,34 @@ class Network:
         _check(load().cortex_get_state(self._h, net_idx, _p(v, ctypes.c_float), _p(c, ctypes.c_float),
                                        _p(r, ctypes.c_int32)), "cortex_get_state")
         return v, c, r
+
+    def ring(self, net_idx: int = 0) -> np.ndarray:
+        """cortex_get_ring: [D, n] float32, row s = input at the step t' in [t, t + D) with
+        t' mod D == s (t the current step)."""
+        spec = self.specs[net_idx]
+        out = np.zeros((spec.d_max + 1, spec.n), np.float32)
+        _check(load().cortex_get_ring(self._h, net_idx, _p(out, ctypes.c_float)), "cortex_get_ring")
+        return out
+
+    def set_state(self, net_idx: int = 0, v=None, i_syn=None, refr=None, ring=None):
+        """cortex_set_state: restore any of V, I, refractory counts and the ring ([D, n])."""
+        n = self.specs[net_idx].n
+        def arr(x, dt, shape):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dt)
+            if a.shape != shape:
+                raise ValueError(f"expected shape {shape}, got {a.shape}")
+            return a
+        v = arr(v, np.float32, (n,))
+        c = arr(i_syn, np.float32, (n,))
+        r = arr(refr, np.int32, (n,))
+        g = arr(ring, np.float32, (self.specs[net_idx].d_max + 1, n))
+        _check(load().cortex_set_state(self._h, net_idx, _p(v, ctypes.c_float), _p(c, ctypes.c_float),
+                                       _p(r, ctypes.c_int32), _p(g, ctypes.c_float)), "cortex_set_state")
+
+    def set_step(self, step: int):
+        _check(load().cortex_set_step(self._h, int(step)), "cortex_set_step")
 
     def constants(self, net_idx: int = 0):
         out6 = np.zeros(6, np.float32)

@@ -868,6 +868,50 @@ int cortex_get_state(cortex_net* h, int32_t net_idx, float* v, float* i_syn, int
   return CORTEX_OK;
 }
 
+int cortex_get_ring(cortex_net* h, int32_t net_idx, float* ring) {
+  if (!h || !ring || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_get_ring: arguments");
+  const NetDev& d = h->nets_h[net_idx];
+  // each block holds [D][T_b] floats of its targets; the host array is [D][n]
+  for (int g = 0; g < d.n_blocks; ++g) {
+    const BlockWork& w = h->work_h[d.first_block + g];
+    CUDA_TRY(cudaMemcpy2DAsync(ring + w.t0, 4 * (size_t)d.n, h->ring + w.ring_base, 4 * (size_t)w.nt,
+                               4 * (size_t)w.nt, (size_t)d.depth, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_set_state(cortex_net* h, int32_t net_idx, const float* v, const float* i_syn, const int32_t* refr,
+                     const float* ring) {
+  if (!h || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_set_state: arguments");
+  if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_set_state: an earlier device wait timed out; free the handle");
+  const NetDev& d = h->nets_h[net_idx];
+  if (refr)
+    for (int32_t i = 0; i < d.n; ++i)
+      if (refr[i] < 0 || refr[i] > d.n_ref) return fail(CORTEX_ERR_ARG, "cortex_set_state: refractory count outside 0..n_ref");
+  if (v) CUDA_TRY(cudaMemcpyAsync(h->V + d.neuron_base, v, 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
+  if (i_syn) CUDA_TRY(cudaMemcpyAsync(h->I + d.neuron_base, i_syn, 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
+  if (refr) CUDA_TRY(cudaMemcpyAsync(h->R + d.neuron_base, refr, 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
+  if (ring)
+    for (int g = 0; g < d.n_blocks; ++g) {
+      const BlockWork& w = h->work_h[d.first_block + g];
+      CUDA_TRY(cudaMemcpy2DAsync(h->ring + w.ring_base, 4 * (size_t)w.nt, ring + w.t0, 4 * (size_t)d.n,
+                                 4 * (size_t)w.nt, (size_t)d.depth, cudaMemcpyHostToDevice, h->stream));
+    }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_set_step(cortex_net* h, int64_t step) {
+  if (!h || step < 0) return fail(CORTEX_ERR_ARG, "cortex_set_step: arguments");
+  if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_set_step: an earlier device wait timed out; free the handle");
+  const long long st = (long long)step;
+  CUDA_TRY(cudaMemcpyAsync(h->step_counter, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->step = step;
+  return CORTEX_OK;
+}
+
 int cortex_constants(cortex_net* h, int32_t net_idx, float* out6, uint32_t* thr, int32_t* n_thr, int32_t* n_ref) {
   if (!h || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_constants: arguments");
   const NetDev& d = h->nets_h[net_idx];

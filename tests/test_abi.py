@@ -81,3 +81,11 @@ def test_option_checks_before_any_device_call():
                  cortex.make_options(balance=2, net_work=[1.0] * (len(specs) - 1) + [float("nan")])):
         assert L.cortex_build_batch(arr, sd, len(specs), ctypes.byref(opts), None, ctypes.byref(h)) == -1
         assert h.value is None
+
+
+def test_checkpoint_calls_check_their_arguments_without_gpu():
+    L = cortex.load()
+    buf = (ctypes.c_float * 4)()
+    assert L.cortex_get_ring(None, 0, buf) == -1
+    assert L.cortex_set_state(None, 0, None, None, None, None) == -1
+    assert L.cortex_set_step(None, 0) == -1

@@ -214,3 +214,85 @@ def test_autotune_plan_does_not_change_results(cortex):
             assert np.array_equal(s0, s1) and np.array_equal(i0, i1)
     _, os_, oi, _ = oracle_run(specs[0], seeds[0], 600)
     assert first_mismatch(*rasters[0][0], os_, oi) == -1
+
+
+def test_ring_matches_the_oracle_ring(cortex):
+    """The ring of future input after 300 steps (cortex_get_ring, slot-major) equals the oracle's
+    ring (neuron-major, slot = step mod D) element by element; shared-memory and global ring."""
+    cfg = W.CONFIGS["c0"]
+    spec, seed, steps = cfg["spec"], cfg["seed"], 300
+    ref, _, _, _ = oracle_run(spec, seed, steps)
+    oring = ref.ring()
+    assert np.count_nonzero(oring) > 0
+    for ring_mode in (1, 2):
+        with cortex.Network(spec, seed, cortex.make_options(ring=ring_mode)) as net:
+            net.simulate(steps)
+            g = net.ring()
+        assert g.shape == (spec.d_max + 1, spec.n)
+        assert np.array_equal(g.T.astype(np.float64), oring)
+
+
+def test_checkpoint_restore_continues_bit_exact(cortex):
+    """State (V, I, refractory counts, ring) and step of a batch of networks after 300 steps,
+    restored into fresh handles built from the same params and seeds: the next 300 steps give
+    the same rasters and final states as the uninterrupted run, in both ring modes."""
+    specs, seeds = W.small_batch_specs(n_nets=3)
+    for ring_mode in (1, 2):
+        opts = cortex.make_options(ring=ring_mode)
+        with cortex.Network(specs, seeds, opts) as a:
+            a.simulate(300)
+            ck = [(a.state(b), a.ring(b)) for b in range(len(specs))]
+            a.clear_spikes()
+            a.simulate(300)
+            ra = [a.spikes(b) for b in range(len(specs))]
+            sa = [a.state(b) for b in range(len(specs))]
+        with cortex.Network(specs, seeds, opts) as b_net:
+            for b, ((v, c, r), g) in enumerate(ck):
+                b_net.set_state(b, v=v, i_syn=c, refr=r, ring=g)
+            b_net.set_step(300)
+            b_net.simulate(300)
+            for b in range(len(specs)):
+                s1, i1 = b_net.spikes(b)
+                assert np.array_equal(s1, ra[b][0]) and np.array_equal(i1, ra[b][1])
+                assert len(s1) > 0 and s1.min() >= 300
+                for x, y in zip(b_net.state(b), sa[b]):
+                    assert np.array_equal(x, y)
+
+
+def test_restore_from_the_oracle_state(cortex):
+    """The oracle's FP32 state and ring after 200 steps, loaded into a fresh GPU handle at step
+    200: the GPU's next 200 steps equal the oracle's continuation bit for bit.  This pins the
+    checkpoint layout and the step convention against the oracle, not only against the GPU."""
+    cfg = W.CONFIGS["c0"]
+    spec, seed = cfg["spec"], cfg["seed"]
+    ref = orc.Network(oracle_params(spec), seed)
+    ref.simulate(200)
+    v, c, r = ref.state()
+    ring = ref.ring().T
+    s0, _ = ref.raster()
+    ref.simulate(200)
+    s_all, i_all = ref.raster()
+    keep = s_all >= 200
+    with cortex.Network(spec, seed) as net:
+        net.set_state(0, v=v.astype(np.float32), i_syn=c.astype(np.float32), refr=r, ring=ring.astype(np.float32))
+        net.set_step(200)
+        net.simulate(200)
+        gs, gi = net.spikes()
+        gv, gc, gr = net.state()
+    assert len(s0) > 0 and keep.sum() > 0
+    assert first_mismatch(gs, gi, s_all[keep], i_all[keep]) == -1
+    ov, oc, orr = ref.state()
+    assert np.array_equal(gv.astype(np.float64), ov) and np.array_equal(gc.astype(np.float64), oc)
+    assert np.array_equal(gr, orr)
+
+
+def test_set_state_refuses_bad_refractory_counts(cortex):
+    cfg = W.CONFIGS["c0"]
+    with cortex.Network(cfg["spec"], cfg["seed"]) as net:
+        _, _, r = net.state()
+        bad = r.copy()
+        bad[5] = 10_000
+        with pytest.raises(cortex.CortexError):
+            net.set_state(0, refr=bad)
+        with pytest.raises(cortex.CortexError):
+            net.set_step(-1)
