@@ -607,6 +607,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         } while ((w >> 48) != want);
         return w;
       };
+      // First the next window's Poisson table (its first entry is this window's last step, whose I
+      // half runs after the delivery), by every thread: it needs nothing from the other blocks,
+      // whose lines arrive meanwhile.  (Filling it in the warps that do not poll, alongside the
+      // polls, left the warp holding both kinds of lanes on the critical path.)
+      if (do_update) poisson_fill(t0 + Wn - 1, max(min(W, a.n_steps - done - Wn), 1), tid, 1 << 30, blockDim.x);
       for (int b = tid; b < nb && !fail; b += blockDim.x) {
         const unsigned long long* line = a.mbox + ((size_t)par * a.n_blocks + first_block + b) * kMboxWords;
         unsigned long long* ml = mbl + (size_t)b * kMboxWords;
@@ -634,16 +639,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         const int n_idw = (int)((min(tot, inl) + 2u) / 3u);
         for (int j = n_cw + 1; j < n_cw + n_idw && !fail; ++j) ml[j] = poll(line + j, ld_relaxed_u64(line + j));
         if (tot > inl) __threadfence();  // the block's further ids are read from its global list
-      }
-      // the next window's Poisson table (its first entry is this window's last step, whose I half
-      // runs after the delivery): threads that do not poll fill it meanwhile
-      if (do_update) {
-        const int ns = max(min(W, a.n_steps - done - Wn), 1);
-        if ((int)blockDim.x > nb) {
-          if (tid >= nb) poisson_fill(t0 + Wn - 1, ns, tid - nb, 1 << 30, (int)blockDim.x - nb);
-        } else {
-          poisson_fill(t0 + Wn - 1, ns, tid, 1 << 30, blockDim.x);
-        }
       }
       if (__syncthreads_or(fail)) {
         if (tid == 0) atomicOr(a.err, kErrTimeout);
