@@ -189,10 +189,12 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
   if (fixed_t) S = std::min<double>(S, o.targets_per_block);
   for (int iter = 0; iter < 10000; ++iter) {
     int64_t blocks = 0;
+    bool capped = true;  // every network at its largest block already: a larger budget changes nothing
     tb.assign(h->n_nets, 0);
     for (int b = 0; b < h->n_nets; ++b) {
       const int64_t n = (int64_t)h->params[b].n_exc + h->params[b].n_inh;
       int64_t t = std::min<int64_t>(n, std::max<int64_t>(tmin, (int64_t)(S / cost[b])));
+      capped = capped && (t >= n || (!fixed_t && t >= tcap[b]));
       if (!fixed_t) t = std::min(t, tcap[b]);
       // balance the blocks of one network
       const int64_t nb = ceil_div(n, t);
@@ -204,6 +206,10 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
     for (int b = 0; b < h->n_nets; ++b) ok = ok && tb[b] <= 65535;
     if (!ok) return fail(CORTEX_ERR_UNSUPPORTED, "targets per block above 65535 (network too large for one GPU plan)");
     if (blocks <= cap || fixed_t) return CORTEX_OK;
+    if (capped)
+      return fail(CORTEX_ERR_UNSUPPORTED, "the networks need " + std::to_string(blocks) + " blocks of at most the " +
+                                              "targets shared memory allows, more than the " + std::to_string(cap) +
+                                              " SMs (too large for one GPU plan)");
     S += std::max(1.0, std::floor(S / 16));
   }
   return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
