@@ -130,6 +130,15 @@ int cortex_build(const cortex_params* params, uint64_t seed, const cortex_option
 int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32_t n_nets,
                        const cortex_options* opts, void* stream, cortex_net** out);
 
+/* The block plan cortex_build_batch makes (the domain decomposition of Sec. II-B: targets per
+ * block, Eq. 9-10), computed on the host alone with no device call: for a GPU with n_sm SMs and
+ * smem_per_block bytes of opt-in dynamic shared memory per block, targets_out[b] receives the
+ * targets per block of network b (its last block may hold fewer) and *n_blocks_out (may be NULL)
+ * the block count.  Same options and errors as the build's planning step: CORTEX_ERR_ARG,
+ * CORTEX_ERR_UNSUPPORTED (no plan fits the SMs). */
+int cortex_plan(const cortex_params* params, int32_t n_nets, const cortex_options* opts,
+                int32_t n_sm, int64_t smem_per_block, int32_t* targets_out, int32_t* n_blocks_out);
+
 /* Autotuner (the paper has no counterpart: its partition is fixed by processes and threads).
  * Builds the network(s) of params / seeds with each candidate plan -- warps per block, i.e. the
  * number and width of the per-warp indegree sub-graphs (Sec. III-B), in {8, 10, 12, 14}, times the

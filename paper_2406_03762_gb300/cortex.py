@@ -70,7 +70,7 @@ EXPORTED = [
     "cortex_build", "cortex_build_batch", "cortex_simulate", "cortex_spikes", "cortex_clear_spikes",
     "cortex_stats", "cortex_export_synapses", "cortex_get_state", "cortex_constants", "cortex_deliver",
     "cortex_philox", "cortex_free", "cortex_strerror", "cortex_last_error", "cortex_subgraph_noalloc",
-    "cortex_autotune", "cortex_get_ring", "cortex_set_state", "cortex_set_step",
+    "cortex_autotune", "cortex_get_ring", "cortex_set_state", "cortex_set_step", "cortex_plan",
 ]
 
 _lib = None
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = False):
     L.cortex_set_state.argtypes = [vp, ctypes.c_int32, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_int32),
                                    P(ctypes.c_float)]
     L.cortex_set_step.argtypes = [vp, ctypes.c_int64]
+    L.cortex_plan.argtypes = [P(Params), ctypes.c_int32, P(Options), ctypes.c_int32, ctypes.c_int64, P(ctypes.c_int32),
+                              P(ctypes.c_int32)]
     L.cortex_autotune.argtypes = [P(Params), P(ctypes.c_uint64), ctypes.c_int32, P(Options), ctypes.c_int32, vp,
                                   P(Options), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_float)]
     for name in EXPORTED:
@@ -193,6 +195,20 @@ def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000,
     else:
         best.net_work = None
     return best, float(ms.value), int(n.value)
+
+
+def plan(specs, options: Options | None = None, n_sm: int = 152, smem_per_block: int = 232448):
+    """cortex_plan: (targets per block of each network, block count) for a GPU with n_sm SMs and
+    smem_per_block bytes of opt-in shared memory per block; host only."""
+    L = load()
+    if not isinstance(specs, (list, tuple)):
+        specs = [specs]
+    arr = (Params * len(specs))(*[params_from_spec(s) for s in specs])
+    tb = np.zeros(len(specs), np.int32)
+    nb = ctypes.c_int32(0)
+    _check(L.cortex_plan(arr, len(specs), ctypes.byref(options) if options is not None else None, int(n_sm),
+                         int(smem_per_block), _p(tb, ctypes.c_int32), ctypes.byref(nb)), "cortex_plan")
+    return tb, int(nb.value)
 
 
 class Network:

@@ -215,6 +215,28 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
   return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
 }
 
+// parameters of every network and the options, checked before anything is allocated
+int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_options& o) {
+  for (int b = 0; b < n_nets; ++b) {
+    std::string why;
+    int rc = validate_params(params[b], why);
+    if (rc != CORTEX_OK) return fail(rc, "network " + std::to_string(b) + ": " + why);
+    if (params[b].weight_dtype != params[0].weight_dtype)
+      return fail(CORTEX_ERR_UNSUPPORTED, "all networks of a batch must use the same weight_dtype");
+  }
+  if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..14");
+  if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
+  if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
+  if (o.balance < 0 || o.balance > 2) return fail(CORTEX_ERR_ARG, "balance");
+  if (o.balance == 2) {
+    if (!o.net_work) return fail(CORTEX_ERR_ARG, "balance 2 needs net_work");
+    for (int b = 0; b < n_nets; ++b)
+      if (!(o.net_work[b] > 0.0f) || !std::isfinite(o.net_work[b])) return fail(CORTEX_ERR_ARG, "net_work must be finite and > 0");
+  }
+  if (o.spikes_per_round < 0 || o.spikes_per_round > kSpikeBatch) return fail(CORTEX_ERR_ARG, "spikes_per_round must be 0..32");
+  return CORTEX_OK;
+}
+
 int check_err(cortex_net* h, const char* where) {
   int32_t e = 0;
   CUDA_TRY(cudaMemcpyAsync(&e, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
@@ -460,23 +482,8 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   cortex_options o;
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  for (int b = 0; b < n_nets; ++b) {
-    std::string why;
-    int rc = validate_params(params[b], why);
-    if (rc != CORTEX_OK) return fail(rc, "network " + std::to_string(b) + ": " + why);
-    if (params[b].weight_dtype != params[0].weight_dtype)
-      return fail(CORTEX_ERR_UNSUPPORTED, "all networks of a batch must use the same weight_dtype");
-  }
-  if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..14");
-  if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
-  if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
-  if (o.balance < 0 || o.balance > 2) return fail(CORTEX_ERR_ARG, "balance");
-  if (o.balance == 2) {
-    if (!o.net_work) return fail(CORTEX_ERR_ARG, "balance 2 needs net_work");
-    for (int b = 0; b < n_nets; ++b)
-      if (!(o.net_work[b] > 0.0f) || !std::isfinite(o.net_work[b])) return fail(CORTEX_ERR_ARG, "net_work must be finite and > 0");
-  }
-  if (o.spikes_per_round < 0 || o.spikes_per_round > kSpikeBatch) return fail(CORTEX_ERR_ARG, "spikes_per_round must be 0..32");
+  int rc = check_inputs(params, n_nets, o);
+  if (rc != CORTEX_OK) return rc;
 
   cortex_net* h = new (std::nothrow) cortex_net();
   if (!h) return fail(CORTEX_ERR_OOM, "handle");
@@ -504,7 +511,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   h->withhold_block = o.test_withhold_block > 0 ? o.test_withhold_block - 1 : -1;
 
   std::vector<int32_t> tb;
-  int rc = plan_blocks(h, o, tb);
+  rc = plan_blocks(h, o, tb);
   if (rc != CORTEX_OK) return bail(rc);
 
   // networks and the work table
@@ -673,6 +680,34 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   }
 #undef TRY
   *out = h;
+  return CORTEX_OK;
+}
+
+int cortex_plan(const cortex_params* params, int32_t n_nets, const cortex_options* opts, int32_t n_sm,
+                int64_t smem_per_block, int32_t* targets_out, int32_t* n_blocks_out) {
+  if (!params || n_nets <= 0 || n_sm <= 0 || smem_per_block <= 1024 || !targets_out)
+    return fail(CORTEX_ERR_ARG, "cortex_plan: arguments");
+  cortex_options o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  int rc = check_inputs(params, n_nets, o);
+  if (rc != CORTEX_OK) return rc;
+  cortex_net h;  // host fields only: nothing is allocated on the device
+  h.n_sm = n_sm;
+  h.smem_cap = (size_t)smem_per_block - 1024;  // as the build: room for static shared memory
+  h.n_nets = n_nets;
+  h.params.assign(params, params + n_nets);
+  h.wdtype = params[0].weight_dtype;
+  h.n_warps = o.warps_per_block ? o.warps_per_block : 14;
+  std::vector<int32_t> tb;
+  rc = plan_blocks(&h, o, tb);
+  if (rc != CORTEX_OK) return rc;
+  int64_t blocks = 0;
+  for (int b = 0; b < n_nets; ++b) {
+    targets_out[b] = tb[b];
+    blocks += ceil_div((int64_t)params[b].n_exc + params[b].n_inh, tb[b]);
+  }
+  if (n_blocks_out) *n_blocks_out = (int32_t)blocks;
   return CORTEX_OK;
 }
 

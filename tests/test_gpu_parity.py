@@ -296,3 +296,17 @@ def test_set_state_refuses_bad_refractory_counts(cortex):
             net.set_state(0, refr=bad)
         with pytest.raises(cortex.CortexError):
             net.set_step(-1)
+
+
+def test_host_plan_matches_the_build(cortex):
+    """cortex_plan (host only) gives the block count the build makes on this GPU."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    smem = getattr(props, "shared_memory_per_block_optin", 232448)
+    specs, seeds = W.small_batch_specs()
+    for kw in (dict(), dict(balance=1), dict(balance=2, net_work=[20.0, 1.0, 0.5, 3.0, 1.0, 8.0]),
+               dict(warps_per_block=8)):
+        opts = cortex.make_options(**kw)
+        _, nb = cortex.plan(specs, opts, n_sm=props.multi_processor_count, smem_per_block=smem)
+        with cortex.Network(specs, seeds, opts) as net:
+            assert net.stats()["n_blocks"] == nb, kw
