@@ -332,23 +332,11 @@ __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ net
       }
       e_w = lo;
     }
-    // cells repeated inside a warp's piece (a source drawn twice by one target with one delay):
-    // flag the warp, whose delivery then adds that piece one entry at a time
-    __syncwarp();
-    uint32_t dup = 0;
-    for (uint32_t q = lane; q + 1 < len; q += 32) {
-      const uint32_t local = buf[q] >> 16;
-      for (uint32_t q2 = q + 1; q2 < len && (buf[q2] >> 16) == local; ++q2) {
-        const uint32_t j1 = buf[q] & 0xffffu, j2 = buf[q2] & 0xffffu;
-        const Draw2 d1 = draw_pair(d, (uint32_t)w.t0 + local, j1 >> 1);
-        const Draw2 d2 = draw_pair(d, (uint32_t)w.t0 + local, j2 >> 1);
-        if (d1.dly[j1 & 1u] == d2.dly[j2 & 1u]) dup |= 1u << (local / (uint32_t)w.tw);
-      }
-    }
-    dup = __reduce_or_sync(0xffffffffu, dup);
+    // (a cell repeated inside a piece -- a source drawn twice by one target with one delay -- needs
+    // no mark: the delivery orders equal cells of a chunk by lane, i.e. in record order)
     if (piece + len > 0xffffu && lane == 0) atomicOr(err, kErrSegment);  // rows longer than 65535
     uint32_t words[8];
-    words[0] = (piece & 0xffffu) | (dup << 16);
+    words[0] = piece & 0xffffu;  // high half reserved (zero)
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       const uint32_t x = __shfl_sync(0xffffffffu, e_w, 2 * q);
