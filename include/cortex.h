@@ -72,7 +72,7 @@ typedef struct cortex_params {
 typedef struct cortex_options {
   int32_t ring;                      /* CORTEX_RING_* */
   int32_t mode;                      /* CORTEX_MODE_* */
-  int32_t warps_per_block;           /* 0 = auto; 1..14 */
+  int32_t warps_per_block;           /* 0 = auto (14); 1..16 */
   int32_t targets_per_block;         /* 0 = auto; upper bound on targets owned by one block */
   int32_t steps_per_launch;          /* 0 = auto; steps per persistent launch (graph node) */
   int32_t use_graph;                 /* 0 = auto (on), 1 = on, -1 = off */
@@ -141,7 +141,7 @@ int cortex_plan(const cortex_params* params, int32_t n_nets, const cortex_option
 
 /* Autotuner (the paper has no counterpart: its partition is fixed by processes and threads).
  * Builds the network(s) of params / seeds with each candidate plan -- warps per block, i.e. the
- * number and width of the per-warp indegree sub-graphs (Sec. III-B), in {8, 10, 12, 14}, times the
+ * number and width of the per-warp indegree sub-graphs (Sec. III-B), in {8, 10, 12, 14, 16}, times the
  * block plan -- simulates trial_steps > 0 steps after one untimed launch, frees it, and returns
  * in *best the options of the fastest candidate (the other fields copied from base, which may be
  * NULL).  Block plans: balance 0 and 1, and, when net_work_out is not NULL and n_nets > 1,

@@ -146,7 +146,7 @@ int64_t max_block_targets(const cortex_params& p, int wsz, int n_warps, size_t s
     const double lam = (double)t * (double)k / (double)n;
     int cw = 0, cm = 0;
     step_staging_caps((int)std::ceil(lam + 6.0 * std::sqrt(lam) + 16.0), wsz, &cw, &cm);
-    const size_t fixed = step_smem_bytes((int)t, p.d_max + 1, p.d_min + 1, (int)ceil_div(n, t), false, 0);
+    const size_t fixed = step_smem_bytes((int)t, p.d_max + 1, p.d_min + 1, (int)ceil_div(n, t), false, 0, n_warps);
     return fixed + (size_t)2 * kStages * (cw + cm) <= smem_cap;
   };
   int64_t lo = std::min<int64_t>(n, 32ll * n_warps), hi = std::min<int64_t>(n, 65535);
@@ -224,7 +224,7 @@ int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_optio
     if (params[b].weight_dtype != params[0].weight_dtype)
       return fail(CORTEX_ERR_UNSUPPORTED, "all networks of a batch must use the same weight_dtype");
   }
-  if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..14");
+  if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..16");
   if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
   if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
   if (o.balance < 0 || o.balance > 2) return fail(CORTEX_ERR_ARG, "balance");
@@ -400,7 +400,7 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   std::vector<size_t> per(nn);  // staging bytes per spike of a round (kStages rounds in flight)
   auto layout = [&](int b, bool ring, size_t stage) {
     const NetDev& d = h->nets_h[b];
-    return step_smem_bytes(h->work_h[d.first_block].nt, d.depth, d.window, d.n_blocks, ring, (int)stage);
+    return step_smem_bytes(h->work_h[d.first_block].nt, d.depth, d.window, d.n_blocks, ring, (int)stage, h->n_warps);
   };
   auto room = [&](int b, bool ring) -> size_t {  // staging bytes that fit next to the rest
     const size_t fixed = layout(b, ring, 0);
@@ -729,7 +729,7 @@ int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t 
     int balance, warps;
     float update_cost;
   };
-  const int warps[] = {8, 10, 12, 14};
+  const int warps[] = {8, 10, 12, 14, 16};
   std::vector<Cand> cands;
   for (int bal = 0; bal <= 1; ++bal)
     for (int w : warps) cands.push_back({bal, w, 0.0f});

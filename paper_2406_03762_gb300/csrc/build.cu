@@ -246,6 +246,7 @@ cudaError_t launch_build_fill_net(const NetDev* nets_dev, int net_idx, int32_t n
 // Record of synapse (source s -> local target j, delay d): weight w and
 //   meta = ((j - wd * tw) << dbits) | (d - d_min),   wd = j / tw the delivery warp owning j.
 constexpr int kSegCap = 2048;  // keys sorted in shared memory per warp
+static_assert(kSegCap <= (int)kMaxPiece, "piece ends are 12-bit header fields");
 
 __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ nets, const BlockWork* __restrict__ work,
                                                   int net_idx, int first_group, int n_groups, int n_dw,
@@ -335,15 +336,14 @@ __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ net
     // (a cell repeated inside a piece -- a source drawn twice by one target with one delay -- needs
     // no mark: the delivery orders equal cells of a chunk by lane, i.e. in record order)
     if (piece + len > 0xffffu && lane == 0) atomicOr(err, kErrSegment);  // rows longer than 65535
-    uint32_t words[8];
-    words[0] = piece & 0xffffu;  // high half reserved (zero)
+    uint32_t words[8] = {piece & 0xffffu, 0u, 0u, 0u, 0u, 0u, 0u, 0u};  // high half of word 0 reserved
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const uint32_t x = __shfl_sync(0xffffffffu, e_w, 2 * q);
-      const uint32_t y = __shfl_sync(0xffffffffu, e_w, 2 * q + 1);
-      const uint32_t ex = (2 * q < n_dw) ? x : len;
-      const uint32_t ey = (2 * q + 1 < n_dw) ? y : len;
-      words[q + 1] = (ex & 0xffffu) | (ey << 16);
+    for (int q = 0; q < kMaxWarps; ++q) {  // end[q] as the 12-bit field at bit 32 + 12 q
+      const uint32_t x = __shfl_sync(0xffffffffu, e_w, q);
+      const uint32_t e = (q < n_dw) ? x : len;
+      const int p = 32 + 12 * q, i = p >> 5, sh = p & 31;
+      words[i] |= e << sh;
+      if (sh > 20) words[i + 1] |= e >> (32 - sh);
     }
     if (lane == 0) {
       const int64_t h = hdr_net + (int64_t)src * nbk + (first_group + g);
@@ -427,8 +427,7 @@ __global__ void k_export(const NetDev* __restrict__ nets, const BlockWork* __res
     const uint32_t base = words[0] & 0xffffu;
     uint32_t e0 = 0;
     for (int wd = 0; wd < n_dw; ++wd) {
-      const uint32_t word = words[1 + (wd >> 1)];
-      const uint32_t e1 = (wd & 1) ? (word >> 16) : (word & 0xffffu);
+      const uint32_t e1 = hdr_end(words, wd);
       for (uint32_t q = e0; q < e1; ++q) {
         const int64_t r = d.rec_base + (int64_t)row_base[d.row_off + s] + base + q;
         const uint32_t meta = rec_meta[r];

@@ -9,9 +9,9 @@
 //             All blocks read adjacent pieces of one spiking source's row (shared pages and rows).
 //   row_base  u64 per source: first record of the source's row, relative to the network's base.
 //   headers   one 32-byte header per (source, block), stored source-major: word 0 = first record of
-//             the block's piece relative to the row (low 16 bits) | flags (bit 16 + w: warp w's piece
-//             repeats a cell; informational), then u16 end[w] for the block's delivery warps
-//             w = 0..13 (entries of warps 0..w; unused entries repeat the total).
+//             the block's piece relative to the row (low 16 bits; the high half is reserved), then
+//             sixteen 12-bit fields end[w] for the delivery warps w = 0..15 (entries of warps
+//             0..w; the fields of absent warps repeat the total) -- see hdr_end.
 //   state     V (f32), I (f32), refractory counter (i32) per neuron.
 //   ring      per block [D][T_b] floats, D = d_max + 1: cell (slot, j) holds the input due at the
 //             step t with t mod D == slot for local target j.
@@ -28,7 +28,20 @@
 namespace cortex {
 
 constexpr int kPoissonCap = 64;     // Poisson threshold table entries
-constexpr int kMaxWarps = 14;       // warps per block, all of them delivery warps (32-byte header: 4 + 2 * 14)
+constexpr int kMaxWarps = 16;       // warps per block, all of them delivery warps (one 12-bit end each in the header)
+constexpr int kNarrowWarps = 14;    // blocks of up to this many warps run a kernel built for them
+                                     // (448 threads: up to 146 registers a thread instead of 128)
+constexpr uint32_t kMaxPiece = 4095;  // entries of one (source, block) piece: the ends are 12-bit fields
+
+// The 32-byte header of a (source, block) piece, as eight 32-bit words: bits 0-15 of word 0 are
+// the piece's offset in the source's row; from bit 32 on, sixteen 12-bit fields hold end[w], the
+// end (exclusive, in entries from the piece start) of delivery warp w's sub-range; the fields of
+// warps the block does not have hold the piece length, so end[kMaxWarps - 1] is the length.
+__host__ __device__ inline uint32_t hdr_end(const uint32_t* words, int w) {
+  const int p = 32 + 12 * w, i = p >> 5, s = p & 31;  // i + 1 <= 7 for w < 16
+  const unsigned long long x = ((unsigned long long)words[i + 1] << 32) | words[i];
+  return (uint32_t)(x >> s) & 0xfffu;
+}
 constexpr int kSpikeBatch = 32;     // spikes staged per delivery round (at most)
 constexpr int kStages = 4;          // delivery rounds in flight per block
 constexpr int kHdrAhead = 2 * kStages - 1;        // headers are fetched this many rounds ahead
@@ -287,7 +300,7 @@ cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, b
 cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s);
 // dynamic shared memory of a block of a network: nt targets per block (its largest block),
 // ring depth, window steps, nb blocks, staging bytes
-size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes);
+size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes, int n_warps);
 void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m);
 cudaError_t step_kernel_attributes(size_t smem);
 int step_occupancy(int threads, size_t smem, bool ring_smem);

@@ -51,7 +51,7 @@ __host__ __device__ inline uint32_t align_to(uint32_t x, uint32_t a) { return (x
 constexpr int kTagHash = 2048;
 
 __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window, int nb, bool ring_smem,
-                                                  int stage_bytes) {
+                                                  int stage_bytes, int n_warps) {
   SmemLayout L;
   uint32_t o = 0;
   L.ring = o;
@@ -89,14 +89,14 @@ __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window,
   L.hdr = o;   // fetched headers: kHdrSlots rounds of (32-byte header, 8-byte row start, pad) per spike
   o += kHdrSlots * kSpikeBatch * 48;
   L.desc = o;  // piece descriptors, kStages + 1 rounds: 32 bytes per spike (copy), then per round
-  o += (kStages + 1) * kSpikeBatch * 32;  //   u32 aux[spike] and u16 end[warp][spike] (fold)
+  o += (kStages + 1) * kSpikeBatch * 32;  //   u32 aux[spike] and u16 end[warp][spike] (fold; from the 12-bit fields)
   L.dsoa = o;
   o += (kStages + 1) * kSpikeBatch * (4 + 2 * kMaxWarps);
   L.perm = o;
   o += kMaxWarps * 32;
   o = align_to(o, 16);
   L.tags = o;
-  o += ring_smem ? align_to((uint32_t)(depth * nt), 16) : (uint32_t)(kMaxWarps * kTagHash);
+  o += ring_smem ? align_to((uint32_t)(depth * nt), 16) : (uint32_t)(n_warps * kTagHash);
   o = align_to(o, 128);
   L.mbl = o;   // mailbox lines read at the barrier: one per block of the network
   o += (uint32_t)(nb * kMboxWords * 8);
@@ -282,8 +282,8 @@ __device__ __forceinline__ void fold_four(float* ring, uint8_t* wtags, const uin
 // a barrier per window inside one cooperative launch of n_steps steps).  kRingSmem: the block's
 // ring slice lives in shared memory for the whole launch (loaded in the prologue, written back
 // in the epilogue); otherwise it is updated in place in global memory.
-template <bool kRingSmem, bool kBf16>
-__global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
+template <bool kRingSmem, bool kBf16, bool kWide>
+__global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_step(const StepArgs a) {
   constexpr uint32_t kWsz = kBf16 ? 2u : 4u;  // bytes per stored weight
   // neuron chunks per update iteration: a global ring is read from L2, so several reads are kept
   // in flight; a shared ring is read with low latency and small per-warp ranges favour one
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
   const uint32_t B = (uint32_t)ndg.batch, cap_w = (uint32_t)ndg.cap_w, cap = (uint32_t)(ndg.cap_w + ndg.cap_m);
 
   // the network's own layout (its blocks' targets, depth, window and block count)
-  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes);
+  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes, n_warps);
   float* ring_s = reinterpret_cast<float*>(smem + L.ring);
   float* sV = reinterpret_cast<float*>(smem + L.sv);
   float* sI = reinterpret_cast<float*>(smem + L.si);
@@ -781,11 +781,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
       auto store_desc = [&](uint32_t x, uint32_t k) {
         const unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
         const uint4 h0 = *reinterpret_cast<const uint4*>(h), h1 = *reinterpret_cast<const uint4*>(h + 16);
+        const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
         const unsigned long long row = *reinterpret_cast<const unsigned long long*>(h + 32);
         const uint32_t g = x * B + k;
         int ws = 0;
         while (ws + 1 < Wn && woffs[ws + 1] <= g) ++ws;
-        const uint32_t len = h1.w >> 16;
+        const uint32_t len = hdr_end(hw, kMaxWarps - 1);
         const unsigned long long r0 = (unsigned long long)rec_net + row + (h0.x & 0xffffu);
         const unsigned long long wbyte = r0 * kWsz, mbyte = r0 * 2ull;
         const uint32_t wal = (uint32_t)(wbyte & 15u), mal = (uint32_t)(mbyte & 15u);
@@ -798,12 +799,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) k_step(const StepArgs a) {
         d[1] = make_uint4(nw | (nm << 16), 0u, 0u, 0u);
         aux_slot(x)[k] = wal | (mal << 8) | ((uint32_t)((tm0 + ws) % D) << 16);
         uint16_t* en = ends_slot(x) + k;
-        const uint32_t hw[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
-        for (int q = 0; q < 7; ++q) {
-          en[(2 * q) * kSpikeBatch] = (uint16_t)(hw[q] & 0xffffu);
-          en[(2 * q + 1) * kSpikeBatch] = (uint16_t)(hw[q] >> 16);
-        }
+        for (int q = 0; q < kMaxWarps; ++q)
+          if (q < n_warps) en[q * kSpikeBatch] = (uint16_t)hdr_end(hw, q);
       };
       // stage the records of round x: warp w copies spikes w, w + n_warps, ...; lane c copies the
       // 16-byte chunk c of the weight piece followed by the meta piece
@@ -994,9 +992,20 @@ __global__ void k_advance(const StepArgs a, int n_nets, int wn) {
   if (net == 0) *a.step_counter += wn;
 }
 
+// the kernel variant for a launch: ring placement, weight type, and whether the block is wider
+// than kNarrowWarps warps
+using StepKernel = void (*)(StepArgs);
+StepKernel step_kernel(bool ring_smem, bool bf16, int threads) {
+  const bool wide = threads > kNarrowWarps * 32;
+  if (wide)
+    return ring_smem ? (bf16 ? k_step<true, true, true> : k_step<true, false, true>)
+                     : (bf16 ? k_step<false, true, true> : k_step<false, false, true>);
+  return ring_smem ? (bf16 ? k_step<true, true, false> : k_step<true, false, false>)
+                   : (bf16 ? k_step<false, true, false> : k_step<false, false, false>);
+}
+
 cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s) {
-  void (*kern)(StepArgs) = a.ring_smem ? (a.bf16 ? k_step<true, true> : k_step<true, false>)
-                                       : (a.bf16 ? k_step<false, true> : k_step<false, false>);
+  StepKernel kern = step_kernel(a.ring_smem != 0, a.bf16 != 0, threads);
   if (cooperative) {
     // all blocks must be co-resident: they wait on each other at the window barrier
     cudaLaunchConfig_t cfg = {};
@@ -1020,8 +1029,8 @@ cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStre
   return cudaGetLastError();
 }
 
-size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes) {
-  return make_layout(nt, depth, window, nb, ring_smem, stage_bytes).total;
+size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes, int n_warps) {
+  return make_layout(nt, depth, window, nb, ring_smem, stage_bytes, n_warps).total;
 }
 
 // staging bytes per spike: a segment of up to max_seg_len records, widened to 16-byte boundaries
@@ -1031,7 +1040,9 @@ void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m) {
 }
 
 cudaError_t step_kernel_attributes(size_t smem) {
-  void (*kerns[4])(StepArgs) = {k_step<true, false>, k_step<true, true>, k_step<false, false>, k_step<false, true>};
+  const StepKernel kerns[8] = {k_step<true, false, false>, k_step<true, true, false>, k_step<false, false, false>,
+                               k_step<false, true, false>,  k_step<true, false, true>, k_step<true, true, true>,
+                               k_step<false, false, true>,  k_step<false, true, true>};
   for (auto k : kerns) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1041,8 +1052,8 @@ cudaError_t step_kernel_attributes(size_t smem) {
 
 int step_occupancy(int threads, size_t smem, bool ring_smem) {
   int n = 0;
-  cudaError_t e = ring_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<true, false>, threads, smem)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, false>, threads, smem);
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel(ring_smem, false, threads), threads, smem);
   return e == cudaSuccess ? n : 0;
 }
 

@@ -100,6 +100,7 @@ MODES = [
     dict(mode=1),                                      # split update / delivery launches
     dict(warps_per_block=4, steps_per_launch=97),      # other warp split, odd launch chunks
     dict(warps_per_block=14, use_graph=-1),
+    dict(warps_per_block=16, ring=2),                  # the widest block: 16 sub-range ends per header
 ]
 
 
@@ -198,7 +199,7 @@ def test_autotune_plan_does_not_change_results(cortex):
     specs, seeds = W.small_batch_specs()
     best, ms, n = cortex.autotune(specs, seeds, trial_steps=200)
     assert n >= 20 and ms > 0
-    assert best.warps_per_block in (8, 10, 12, 14) and best.balance in (0, 1, 2)
+    assert best.warps_per_block in (8, 10, 12, 14, 16) and best.balance in (0, 1, 2)
     if best.balance == 2:
         assert len(best.work()) == len(specs) and min(best.work()) > 0
     uneven = cortex.make_options(warps_per_block=10, balance=2, net_work=[20.0, 1.0, 0.5, 3.0, 1.0, 8.0])
