@@ -42,8 +42,8 @@ extern "C" {
 #define CORTEX_ERR_OVERFLOW (-6)     /* an output buffer was too small (needed size returned) */
 
 /* synaptic weight storage */
-#define CORTEX_F32 0                 /* float weights (7 bytes per synapse with target, delay) */
-#define CORTEX_BF16 1                /* bfloat16 weights, round-to-nearest-even (5 bytes) */
+#define CORTEX_F32 0                 /* float weights: 6 stored bytes per synapse (weight, u16 target/delay) */
+#define CORTEX_BF16 1                /* bfloat16 weights, round-to-nearest-even: 4 stored bytes */
 
 /* ring-buffer placement (cortex_options.ring) */
 #define CORTEX_RING_AUTO 0
@@ -107,8 +107,9 @@ typedef struct cortex_stats_t {
   int32_t ring_in_smem;              /* 1 if the ring lives in shared memory */
   int32_t mode;                      /* CORTEX_MODE_* in use */
   int64_t device_bytes;              /* device memory held by the handle */
-  int32_t spikes_per_round;          /* spikes staged per delivery round */
-  int32_t smem_bytes;                /* dynamic shared memory per block of the step kernel */
+  int32_t spikes_per_round;          /* spikes staged per delivery round (fewest over a batch) */
+  int32_t smem_bytes;                /* dynamic shared memory per block of the step kernel
+                                        (the largest network layout of a batch) */
 } cortex_stats_t;
 
 typedef struct cortex_net cortex_net;
@@ -119,8 +120,9 @@ typedef struct cortex_net cortex_net;
  * per-block sub-graphs, CSR by source inside each block (Eq. 5, Eq. 9-10, Sec. III-B).
  * stream: cudaStream_t or NULL.  opts may be NULL.  On success *out owns all device memory.
  * Errors: CORTEX_ERR_ARG (invalid parameters), CORTEX_ERR_UNSUPPORTED (sizes beyond the
- * layout limits: in-degree or targets per block > 65535, d_max > 255), CORTEX_ERR_OOM,
- * CORTEX_ERR_CUDA.  On error *out is NULL and nothing is leaked. */
+ * layout limits: in-degree or targets per block > 65535, d_max > 255, more than 2,048 synapses
+ * from one source into one block, no block plan within the SMs and their shared memory),
+ * CORTEX_ERR_OOM, CORTEX_ERR_CUDA.  On error *out is NULL and nothing is leaked. */
 int cortex_build(const cortex_params* params, uint64_t seed, const cortex_options* opts,
                  void* stream, cortex_net** out);
 
