@@ -367,19 +367,28 @@ def _form(cortex, W, name, args, stream, peak, peak_kind):
     return out
 
 
+def kernel_digest() -> str:
+    """sha256 of the step kernel's code (step.cu and cortex_internal.cuh) with comments removed and
+    blank space collapsed: it changes when the kernel's code does, not when a comment does."""
+    import hashlib
+    import re
+    tok = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
+    h = hashlib.sha256()
+    for name in ("step.cu", "cortex_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_03762_gb300", "csrc", name)) as g:
+            text = tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", g.read())
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def _traffic(events_per_launch, spec):
-    """DRAM bytes per launch from the committed ncu summary, scaled by events, if the kernel
-    source is unchanged since the capture; else None."""
+    """DRAM bytes per launch from the committed ncu summary, scaled by events, if the kernel's
+    code is unchanged since the capture; else None."""
     path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        import hashlib
-        h = hashlib.sha256()
-        for name in ("step.cu", "cortex_internal.cuh"):
-            with open(os.path.join(ROOT, "paper_2406_03762_gb300", "csrc", name), "rb") as g:
-                h.update(g.read())
-        if d.get("source_sha256") != h.hexdigest():
+        if d.get("kernel_code_sha256") != kernel_digest():
             return None
         return d["dram_bytes_per_event"] * events_per_launch
     except Exception:

@@ -25,9 +25,11 @@
 // Publication and barrier: each block writes one 128-byte mailbox line per window whose 64-bit
 // words all carry the window's tag (step counts, then up to 45 spike ids), and bulk-prefetches
 // the rows of its spiking neurons into L2; reading every line of the network with the tag is the
-// barrier.  The next window's Poisson draws are made by the threads that do not poll.
+// barrier.  Every thread first makes the next window's Poisson draws (they need nothing from the
+// other blocks), then the threads of the polls read the lines.
 //
-// Delivery runs in rounds of up to kSpikeBatch spikes.  Headers (and row starts) are copied into
+// Delivery runs in rounds of up to kSpikeBatch spikes (per network: as many as its staging
+// layout holds).  Headers (and row starts) are copied into
 // shared memory kHdrAhead rounds ahead; one lane per spike turns them into a piece descriptor
 // (global addresses and 16-byte chunk counts for the copy, spike-minor offsets and per-warp ends
 // for the fold); all warps stage the records of round r + kStages - 1 with 16-byte cp.async copies
