@@ -164,7 +164,8 @@ int64_t max_block_targets(const cortex_params& p, int wsz, int n_warps, size_t s
 // about budget / K targets per block), so that blocks of a batch with uneven in-degrees carry
 // similar delivery work; balance 2, work (a network whose targets cost w each per step gets about
 // budget / w), so that blocks of networks with uneven firing rates finish their steps together.
-// No block exceeds max_block_targets.  The budget grows until the blocks fit on the SMs.
+// No block exceeds max_block_targets.  The budget grows until the blocks fit on the SMs and is
+// then bisected down to the smallest budget that still fits.
 int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb) {
   const int cap = h->n_sm;  // one block per SM
   const int64_t tmin = 32ll * h->n_warps;
@@ -187,10 +188,12 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
   double S = mode == 0 ? (double)std::max<int64_t>(tmin, ceil_div(n_total, cap))
                        : std::max((double)tmin * cmax, std::ceil(total / cap));
   if (fixed_t) S = std::min<double>(S, o.targets_per_block);
-  for (int iter = 0; iter < 10000; ++iter) {
+  // the plan of budget S: targets per block of every network; returns the block count, and
+  // whether every network is at its largest block already (a larger budget changes nothing)
+  auto plan_for = [&](double S, std::vector<int32_t>& out, bool& capped) -> int64_t {
     int64_t blocks = 0;
-    bool capped = true;  // every network at its largest block already: a larger budget changes nothing
-    tb.assign(h->n_nets, 0);
+    capped = true;
+    out.assign(h->n_nets, 0);
     for (int b = 0; b < h->n_nets; ++b) {
       const int64_t n = (int64_t)h->params[b].n_exc + h->params[b].n_inh;
       int64_t t = std::min<int64_t>(n, std::max<int64_t>(tmin, (int64_t)(S / cost[b])));
@@ -199,20 +202,48 @@ int plan_blocks(cortex_net* h, const cortex_options& o, std::vector<int32_t>& tb
       // balance the blocks of one network
       const int64_t nb = ceil_div(n, t);
       t = ceil_div(n, nb);
-      tb[b] = (int32_t)std::min<int64_t>(t, 1 << 30);
+      out[b] = (int32_t)std::min<int64_t>(t, 1 << 30);
       blocks += nb;
     }
-    bool ok = true;
-    for (int b = 0; b < h->n_nets; ++b) ok = ok && tb[b] <= 65535;
-    if (!ok) return fail(CORTEX_ERR_UNSUPPORTED, "targets per block above 65535 (network too large for one GPU plan)");
-    if (blocks <= cap || fixed_t) return CORTEX_OK;
+    return blocks;
+  };
+  auto too_wide = [&](const std::vector<int32_t>& t) {
+    for (int32_t x : t)
+      if (x > 65535) return fail(CORTEX_ERR_UNSUPPORTED, "targets per block above 65535 (network too large for one GPU plan)");
+    return CORTEX_OK;
+  };
+  bool capped = false;
+  int64_t blocks = plan_for(S, tb, capped);
+  if (too_wide(tb) != CORTEX_OK) return CORTEX_ERR_UNSUPPORTED;
+  if (blocks <= cap || fixed_t) return CORTEX_OK;
+  // grow the budget until the blocks fit on the SMs (the block count never grows with the budget),
+  // then bisect between the last budget that did not fit and the first that did: the smallest
+  // budget that fits gives the smallest largest block
+  double lo = S;
+  for (int iter = 0;; ++iter) {
     if (capped)
       return fail(CORTEX_ERR_UNSUPPORTED, "the networks need " + std::to_string(blocks) + " blocks of at most the " +
                                               "targets shared memory allows, more than the " + std::to_string(cap) +
                                               " SMs (too large for one GPU plan)");
+    if (iter == 10000) return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
+    lo = S;
     S += std::max(1.0, std::floor(S / 16));
+    blocks = plan_for(S, tb, capped);
+    if (too_wide(tb) != CORTEX_OK) return CORTEX_ERR_UNSUPPORTED;
+    if (blocks <= cap) break;
   }
-  return fail(CORTEX_ERR_UNSUPPORTED, "could not plan the blocks");
+  std::vector<int32_t> trial;
+  for (int it = 0; it < 64 && S - lo > (mode == 0 ? 1.0 : 1e-9 * S); ++it) {
+    const double mid = mode == 0 ? std::floor((lo + S) / 2) : (lo + S) / 2;
+    bool c2 = false;
+    if (plan_for(mid, trial, c2) <= cap) {
+      S = mid;
+      tb.swap(trial);
+    } else {
+      lo = mid;
+    }
+  }
+  return CORTEX_OK;
 }
 
 // parameters of every network and the options, checked before anything is allocated
