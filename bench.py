@@ -367,18 +367,26 @@ def _form(cortex, W, name, args, stream, peak, peak_kind):
     return out
 
 
-def kernel_digest() -> str:
-    """sha256 of the step kernel's code (step.cu and cortex_internal.cuh) with comments removed and
-    blank space collapsed: it changes when the kernel's code does, not when a comment does."""
+def code_digest(texts) -> str:
+    """sha256 of C/C++/CUDA sources with comments removed and blank space collapsed (string
+    literals kept as written): it changes when the code does, not when a comment does."""
     import hashlib
     import re
     tok = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
     h = hashlib.sha256()
-    for name in ("step.cu", "cortex_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2406_03762_gb300", "csrc", name)) as g:
-            text = tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", g.read())
+    for text in texts:
+        text = tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()
+
+
+def kernel_digest() -> str:
+    """code_digest of the step kernel (step.cu and cortex_internal.cuh)."""
+    texts = []
+    for name in ("step.cu", "cortex_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_03762_gb300", "csrc", name)) as g:
+            texts.append(g.read())
+    return code_digest(texts)
 
 
 def _traffic(events_per_launch, spec):
