@@ -73,7 +73,7 @@ struct cortex_net {
   size_t device_bytes = 0;
   // plan
   int n_warps = 14, threads = 448, n_blocks = 0, n_sm = 0;
-  int w_max = 1, w_split = 1, max_nt = 0, max_depth = 0, max_nb = 0;
+  int w_max = 1, w_split = 1;
   bool ring_smem = false;
   bool ring_red = false;  // global ring adds by the L2 reduction unit (exact for the weights)
   int mode = CORTEX_MODE_PERSISTENT;
@@ -612,10 +612,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
       hdr += d.n;
       ring += (int64_t)d.depth * w.nt;
       h->work_h.push_back(w);
-      h->max_nt = std::max(h->max_nt, w.nt);
     }
-    h->max_nb = std::max(h->max_nb, nbk);
-    h->max_depth = std::max(h->max_depth, d.depth);
     h->w_max = std::max(h->w_max, d.window);
     h->w_split = std::min(h->w_split, d.d_min);
     neuron_base += d.n;
