@@ -360,7 +360,9 @@ def _form(cortex, W, name, args, stream, peak, peak_kind):
            "dtype": "bf16" if bpe == 5 else "f32",
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (persistent)",
-                        "launch_ms": ms / launches}}
+                        "launch_ms": ms / launches,
+                        "traffic": _traffic(ev / launches, cfg.get("spec"), "k_step_c3_traffic.json")
+                        if name == "c3" else None}}
     if plan is not None:
         out["plan"] = plan
     net.close()
@@ -389,10 +391,10 @@ def kernel_digest() -> str:
     return code_digest(texts)
 
 
-def _traffic(events_per_launch, spec):
-    """DRAM bytes per launch from the committed ncu summary, scaled by events, if the kernel's
-    code is unchanged since the capture; else None."""
-    path = os.path.join(ROOT, "profiles", "k_step_traffic.json")
+def _traffic(events_per_launch, spec, record="k_step_traffic.json"):
+    """DRAM bytes per launch from a committed ncu record (profiles/<record>), scaled by events, if
+    the kernel's code is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", record)
     try:
         with open(path) as f:
             d = json.load(f)

@@ -35,12 +35,54 @@ def test_digest_sees_every_code_change():
 
 
 def test_traffic_is_reported_only_for_the_measured_kernel():
-    """The bench scales the committed record's DRAM bytes per event while the record's digest is
+    """The bench scales a committed record's DRAM bytes per event while the record's digest is
     the current kernel code's, and reports null otherwise."""
-    with open(os.path.join(ROOT, "profiles", "k_step_traffic.json")) as f:
-        rec = json.load(f)
-    assert 6.0 < rec["dram_bytes_per_event"] < 8.0  # 6 stored bytes per synapse plus headers
-    if rec["kernel_code_sha256"] == bench.kernel_digest():
-        assert bench._traffic(1e6, None) == rec["dram_bytes_per_event"] * 1e6
-    else:
-        assert bench._traffic(1e6, None) is None
+    for name, lo, hi in (("k_step_traffic.json", 6.0, 8.0),      # f32: 6 stored bytes + headers
+                         ("k_step_c3_traffic.json", 4.4, 20.0)):  # bf16: 4 stored bytes + ring spills
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            rec = json.load(f)
+        assert lo < rec["dram_bytes_per_event"] < hi
+        if rec["kernel_code_sha256"] == bench.kernel_digest():
+            assert bench._traffic(1e6, None, name) == rec["dram_bytes_per_event"] * 1e6
+        else:
+            assert bench._traffic(1e6, None, name) is None
+
+
+class _FakeNet:
+    """Stands in for cortex.Network: counts steps and reports fixed per-step events and time."""
+
+    def __init__(self, *a, **k):
+        self.steps, self.last = 0, 0
+
+    def stats(self):
+        return {"events": 5_818_217 * self.steps, "simulate_ms": 0.0605 * self.last, "n_nets": 1,
+                "n_neurons": 1_000_000, "n_synapses": 11_250_000_000, "build_ms": 1.0, "n_blocks": 152,
+                "ring_in_smem": 0, "spikes_per_round": 26, "smem_bytes": 230_272}
+
+    def simulate(self, n):
+        self.steps += n
+        self.last = n
+
+    def close(self):
+        pass
+
+
+class _FakeCortex:
+    Network = _FakeNet
+
+    @staticmethod
+    def make_options(**kw):
+        return kw
+
+
+def test_bench_form_line_without_gpu():
+    """The BF16 form's dictionary builds (including its traffic lookup) with a stand-in library."""
+    import types
+    from paper_2406_03762_gb300 import workloads as W
+    args = types.SimpleNamespace(steps_per_launch=1000, form_steps=2000)
+    out = bench._form(_FakeCortex, W, "c3", args, None, 6785.2, "measured")
+    r = out["roofline"]
+    assert out["dtype"] == "bf16" and abs(out["rtf"] - 0.605) < 1e-9
+    assert abs(r["achieved"] - 5_818_217 * 1000 * 5 / 0.0605e-3 / 1e9 / 1000) < 1e-6 * r["achieved"]
+    if r["traffic"] is not None:
+        assert abs(r["traffic"] / (5_818_217 * 1000) - 16.19) < 0.01
