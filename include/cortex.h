@@ -50,6 +50,15 @@ extern "C" {
 #define CORTEX_RING_SMEM 1           /* each block keeps its targets' ring in shared memory */
 #define CORTEX_RING_GLOBAL 2         /* the ring stays in global memory (owner-exclusive) */
 
+/* delivery fold (cortex_options.fold).  Every ring cell receives its weights in the order
+ * (emission step, source id, draw index), which fixes the FP32 sum.  When the build proves that
+ * every partial sum of a cell is exact -- every weight an integer multiple of 2^e with e >= -126,
+ * and k_exc |j_exc| + k_inh |j_inh| below 2^24 * 2^e (as stored, e.g. bfloat16 weights) -- no add
+ * rounds, so any order gives the same bits and the fold needs no ordering (EXACT). */
+#define CORTEX_FOLD_AUTO 0           /* EXACT when proven, else ORDERED */
+#define CORTEX_FOLD_ORDERED 1        /* lanes sharing a cell add in stream order (always valid) */
+#define CORTEX_FOLD_EXACT 2          /* order-free adds; the build fails (UNSUPPORTED) unless proven */
+
 /* step-loop modes (cortex_options.mode) */
 #define CORTEX_MODE_PERSISTENT 0     /* one cooperative kernel per chunk, grid barrier inside */
 #define CORTEX_MODE_SPLIT 1          /* an update kernel and a delivery kernel per window */
@@ -89,6 +98,13 @@ typedef struct cortex_options {
                                         returns CORTEX_ERR_TIMEOUT (error path of the barrier) */
   const float* net_work;             /* balance 2: n_nets finite costs > 0 (any common unit), read
                                         by the build only; caller-owned; NULL otherwise */
+  int32_t fold;                      /* CORTEX_FOLD_*: how delivery adds into a ring cell */
+  int32_t l2_persist;                /* ring in global memory: 0 = auto (on), 1 = on, -1 = off.
+                                        On: the launches mark the ring as persisting in L2 (an
+                                        access-policy window), and the build raises the process's
+                                        persisting-L2 limit (cudaLimitPersistingL2CacheSize) to the
+                                        ring's size, at most the device maximum; the previous limit
+                                        is restored when the last handle that raised it is freed */
 } cortex_options;
 
 typedef struct cortex_stats_t {
@@ -110,6 +126,8 @@ typedef struct cortex_stats_t {
   int32_t spikes_per_round;          /* spikes staged per delivery round (fewest over a batch) */
   int32_t smem_bytes;                /* dynamic shared memory per block of the step kernel
                                         (the largest network layout of a batch) */
+  int32_t exact_fold;                /* 1 if the delivery uses order-free adds (CORTEX_FOLD_EXACT) */
+  int64_t l2_persist_bytes;          /* bytes of the ring in the persisting L2 window (0: none) */
 } cortex_stats_t;
 
 typedef struct cortex_net cortex_net;

@@ -628,6 +628,15 @@ void oracle_set_state(oracle_net* net, const double* v, const double* cur, const
   }
 }
 
+/* Overwrite the ring, [n][D] as oracle_ring gives it (checkpoint tests). */
+void oracle_set_ring(oracle_net* net, const double* ring) {
+  size_t nd = (size_t)net->n * (size_t)net->depth;
+  for (size_t c = 0; c < nd; ++c) {
+    if (net->p.precision == ORACLE_FP32) net->ring32[c] = (float)ring[c];
+    else net->ring64[c] = ring[c];
+  }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Replay of a few targets                                                                     */
 /* ------------------------------------------------------------------------------------------ */

@@ -118,6 +118,8 @@ def lib():
         L.oracle_constants_f32.restype = None
         L.oracle_set_state.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32)]
         L.oracle_set_state.restype = None
+        L.oracle_set_ring.argtypes = [vp, P(ctypes.c_double)]
+        L.oracle_set_ring.restype = None
         L.oracle_v0_word.argtypes = [ctypes.c_uint64, ctypes.c_int64]
         L.oracle_v0_word.restype = ctypes.c_uint32
         L.oracle_poisson_word.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
@@ -355,6 +357,13 @@ class Network:
         c = np.ascontiguousarray(cur, np.float64)
         r = np.ascontiguousarray(refr, np.int32)
         lib().oracle_set_state(self._h, _ptr(v, ctypes.c_double), _ptr(c, ctypes.c_double), _ptr(r, ctypes.c_int32))
+
+    def set_ring(self, ring):
+        """Overwrite the ring ([n, D], as ring() returns it)."""
+        g = np.ascontiguousarray(ring, np.float64)
+        if g.shape != (self.n, self.depth):
+            raise ValueError(f"expected shape {(self.n, self.depth)}, got {g.shape}")
+        lib().oracle_set_ring(self._h, _ptr(g, ctypes.c_double))
 
     def ring(self) -> np.ndarray:
         out = np.zeros((self.n, self.depth), np.float64)

@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <climits>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -76,6 +78,11 @@ struct cortex_net {
   int w_max = 1, w_split = 1;
   bool ring_smem = false;
   bool ring_red = false;  // global ring adds by the L2 reduction unit (exact for the weights)
+  bool exact = false;     // every partial sum of a ring cell is exact: order-free adds
+  int e_min = 0;          // exact: every weight is an integer multiple of 2^e_min
+  double exact_bound = 0; // exact: largest |partial sum| of a cell, in units of 2^e_min
+  cudaAccessPolicyWindow apw = {};  // the global ring, persisting in L2 (num_bytes 0: none)
+  bool l2_user = false;   // this handle raised the process's persisting-L2 limit
   int mode = CORTEX_MODE_PERSISTENT;
   int stage_bytes = 0, batch = 32;  // largest staging area, fewest spikes per round (stats)
   size_t smem = 0;
@@ -106,7 +113,8 @@ struct cortex_net {
     return cudaSuccess;
   }
 
-  ~cortex_net() {
+  ~cortex_net();
+  void destroy() {
     if (graph) cudaGraphExecDestroy(graph);
     for (void* p : allocs) cudaFree(p);
     if (ev0) cudaEventDestroy(ev0);
@@ -115,6 +123,102 @@ struct cortex_net {
 };
 
 namespace {
+
+// The persisting-L2 limit is a property of the process's CUDA context: handles that keep a global
+// ring resident raise it, and the last of them to be freed puts back the value found before.
+std::mutex g_l2_mu;
+int g_l2_users = 0;
+size_t g_l2_saved = 0;
+
+void l2_persist_acquire(cortex_net* h, int64_t ring_bytes) {
+  int maxp = 0, maxw = 0;
+  if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, h->device) != cudaSuccess || maxp <= 0 ||
+      maxw <= 0 || ring_bytes <= 0) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_l2_mu);
+  size_t cur = 0;
+  if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (g_l2_users == 0) g_l2_saved = cur;
+  const size_t want = std::min<size_t>((size_t)ring_bytes, (size_t)maxp);
+  if (cur < want) {
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess ||
+        cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+  }
+  ++g_l2_users;
+  h->l2_user = true;
+  const size_t win = std::min<size_t>((size_t)ring_bytes, (size_t)maxw);
+  h->apw.base_ptr = h->ring;
+  h->apw.num_bytes = win;
+  h->apw.hitRatio = (float)std::min(1.0, (double)cur / (double)win);
+  h->apw.hitProp = cudaAccessPropertyPersisting;
+  h->apw.missProp = cudaAccessPropertyStreaming;
+}
+
+void l2_persist_release(cortex_net* h) {
+  if (!h->l2_user) return;
+  std::lock_guard<std::mutex> lk(g_l2_mu);
+  h->l2_user = false;
+  if (--g_l2_users == 0) {
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_saved);
+    cudaGetLastError();
+  }
+}
+
+// w = m * 2^e with m an odd integer (w finite and nonzero); false otherwise
+bool weight_grid(float w, int& e) {
+  if (w == 0.0f || !std::isfinite(w)) return false;
+  int x = 0;
+  const double f = std::frexp((double)w, &x);  // |f| in [0.5, 1)
+  long long m = std::llround(std::ldexp(f, 24));  // exact: a float has 24 significant bits
+  e = x - 24;
+  while ((m & 1) == 0) {
+    m /= 2;
+    ++e;
+  }
+  return true;
+}
+
+// Whether every partial sum of every ring cell is exactly representable in FP32.  A cell receives
+// at most one add per incoming synapse of its target (a synapse's successive arrivals land at
+// different steps, and the cell is cleared when its step consumes it): at most k_exc adds of w_exc
+// and k_inh of w_inh.  With every weight an integer multiple of 2^e_min, every partial sum is an
+// integer multiple of 2^e_min of magnitude at most k_exc |w_exc| + k_inh |w_inh|; when that is at
+// most 2^24 * 2^e_min (and 2^e_min is a normal number) every partial sum is a float, no add rounds,
+// and the order of the adds does not change the result.
+bool prove_exact(const std::vector<NetDev>& nets, int& e_min, double& bound) {
+  e_min = INT_MAX;
+  for (const NetDev& d : nets)
+    for (int q = 0; q < 2; ++q) {
+      const float w = q ? d.w_inh : d.w_exc;
+      const int k = q ? d.k_inh : d.k_exc;
+      int e = 0;
+      if (k == 0 || w == 0.0f) continue;
+      if (!weight_grid(w, e)) return false;
+      e_min = std::min(e_min, e);
+    }
+  if (e_min == INT_MAX) {  // no nonzero weight: every sum is zero
+    e_min = 0;
+    bound = 0;
+    return true;
+  }
+  if (e_min < -126 || e_min + 24 > 127) return false;
+  bound = 0;
+  for (const NetDev& d : nets) {
+    const double b = (double)d.k_exc * std::fabs((double)d.w_exc) + (double)d.k_inh * std::fabs((double)d.w_inh);
+    bound = std::max(bound, std::ldexp(b, -e_min));
+  }
+  return bound <= 16777216.0;
+}
 
 int validate_params(const cortex_params& p, std::string& why) {
   if (p.n_exc < 0 || p.n_inh < 0 || (int64_t)p.n_exc + p.n_inh <= 0) return why = "neuron counts", CORTEX_ERR_ARG;
@@ -265,8 +369,19 @@ int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_optio
       if (!(o.net_work[b] > 0.0f) || !std::isfinite(o.net_work[b])) return fail(CORTEX_ERR_ARG, "net_work must be finite and > 0");
   }
   if (o.spikes_per_round < 0 || o.spikes_per_round > kSpikeBatch) return fail(CORTEX_ERR_ARG, "spikes_per_round must be 0..32");
+  if (o.fold < CORTEX_FOLD_AUTO || o.fold > CORTEX_FOLD_EXACT) return fail(CORTEX_ERR_ARG, "fold must be 0..2");
+  if (o.l2_persist < -1 || o.l2_persist > 1) return fail(CORTEX_ERR_ARG, "l2_persist must be -1, 0 or 1");
   return CORTEX_OK;
 }
+
+}  // namespace
+
+cortex_net::~cortex_net() {
+  l2_persist_release(this);
+  destroy();
+}
+
+namespace {
 
 int check_err(cortex_net* h, const char* where) {
   int32_t e = 0;
@@ -310,6 +425,7 @@ StepArgs make_args(cortex_net* h) {
   a.step_counter = h->step_counter;
   a.timeout_ns = h->timeout_ns;
   a.ring_red = h->ring_red ? 1 : 0;
+  a.exact = h->exact ? 1 : 0;
   a.bf16 = h->wdtype == CORTEX_BF16 ? 1 : 0;
   a.withhold_block = h->withhold_block;
   a.t_fixed = -1;
@@ -321,7 +437,7 @@ cudaError_t launch_persistent(cortex_net* h, int n_steps, cudaStream_t s) {
   a.n_steps = n_steps;
   a.phases = kPhaseUpdate | kPhaseDeliver | kPhaseBarrier;
   a.ring_smem = h->ring_smem ? 1 : 0;
-  return launch_step(a, h->n_blocks, h->threads, h->smem, true, s);
+  return launch_step(a, h->n_blocks, h->threads, h->smem, true, s, &h->apw);
 }
 
 cudaError_t launch_split_window(cortex_net* h, int wn, cudaStream_t s) {
@@ -329,11 +445,11 @@ cudaError_t launch_split_window(cortex_net* h, int wn, cudaStream_t s) {
   a.n_steps = wn;
   a.ring_smem = 0;
   a.phases = kPhaseUpdate;
-  cudaError_t e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s);
+  cudaError_t e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s, &h->apw);
   if (e != cudaSuccess) return e;
   a.phases = kPhaseDeliver;
   a.ring_smem = h->ring_smem ? 1 : 0;  // the delivery launch stages its ring slice in shared memory
-  e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s);
+  e = launch_step(a, h->n_blocks, h->threads, h->smem, false, s, &h->apw);
   if (e != cudaSuccess) return e;
   return launch_advance_split(a, h->n_nets, wn, s);
 }
@@ -706,6 +822,14 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
       if (rc != CORTEX_OK) return bail(rc);
     }
   }
+  {
+    // the fold: order-free adds when every partial sum of a cell is proven exact
+    const bool proven = prove_exact(h->nets_h, h->e_min, h->exact_bound);
+    if (o.fold == CORTEX_FOLD_EXACT && !proven)
+      return bail(fail(CORTEX_ERR_UNSUPPORTED, "fold EXACT: the weights do not make every partial sum of a ring cell exact"));
+    h->exact = proven && o.fold != CORTEX_FOLD_ORDERED;
+  }
+  if (!h->ring_smem && o.l2_persist >= 0) l2_persist_acquire(h, 4 * h->total_ring);
 #undef TRY
   *out = h;
   return CORTEX_OK;
@@ -924,6 +1048,8 @@ int cortex_stats(cortex_net* h, cortex_stats_t* st) {
   st->device_bytes = (int64_t)h->device_bytes;
   st->spikes_per_round = h->batch;
   st->smem_bytes = (int32_t)h->smem;
+  st->exact_fold = h->exact ? 1 : 0;
+  st->l2_persist_bytes = (int64_t)h->apw.num_bytes;
   return CORTEX_OK;
 }
 
@@ -958,6 +1084,23 @@ int cortex_set_state(cortex_net* h, int32_t net_idx, const float* v, const float
   if (refr)
     for (int32_t i = 0; i < d.n; ++i)
       if (refr[i] < 0 || refr[i] > d.n_ref) return fail(CORTEX_ERR_ARG, "cortex_set_state: refractory count outside 0..n_ref");
+  if (ring && h->exact) {
+    // order-free adds stay exact only from cells that are themselves integer multiples of
+    // 2^e_min with room below 2^24 * 2^e_min for a full cell's adds; otherwise the handle
+    // returns to the ordered fold (same results, whatever the restored values)
+    bool ok = true;
+    for (int64_t q = 0; q < (int64_t)d.depth * d.n && ok; ++q) {
+      const double x = std::ldexp((double)ring[q], -h->e_min);
+      ok = std::isfinite(x) && x == std::nearbyint(x) && std::fabs(x) + h->exact_bound <= 16777216.0;
+    }
+    if (!ok) {
+      h->exact = false;
+      if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+      }
+    }
+  }
   if (v) CUDA_TRY(cudaMemcpyAsync(h->V + d.neuron_base, v, 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
   if (i_syn) CUDA_TRY(cudaMemcpyAsync(h->I + d.neuron_base, i_syn, 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
   if (refr) CUDA_TRY(cudaMemcpyAsync(h->R + d.neuron_base, refr, 4ull * d.n, cudaMemcpyHostToDevice, h->stream));
@@ -1090,7 +1233,7 @@ int cortex_deliver(cortex_net* h, int32_t net_idx, const int32_t* ids, int64_t n
   a.raster_id = nullptr;
   a.t_fixed = t_emit;
   CUDA_TRY(cudaEventRecord(h->ev0, h->stream));
-  for (int r = 0; r < reps; ++r) CUDA_TRY(launch_step(a, h->n_blocks, h->threads, h->smem, false, h->stream));
+  for (int r = 0; r < reps; ++r) CUDA_TRY(launch_step(a, h->n_blocks, h->threads, h->smem, false, h->stream, &h->apw));
   CUDA_TRY(cudaEventRecord(h->ev1, h->stream));
   CUDA_TRY(cudaMemcpyAsync(&e1, h->events + net_idx, 8, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));

@@ -125,6 +125,7 @@ struct StepArgs {
   int32_t ring_smem;                  // 1: ring slice in shared memory
   int32_t bf16;                       // 1: weights stored as bf16 (all networks of a handle)
   int32_t ring_red;                   // 1: adds into a global ring use the L2 reduction unit
+  int32_t exact;                      // 1: every partial sum of a ring cell is exact (order-free adds)
   long long timeout_ns;
   int32_t withhold_block;             // test hook: this block never publishes (-1: none)
   // delivery-only launches (cortex_deliver): fixed emission step
@@ -166,19 +167,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// loads that bypass L1 (data written by other blocks during the same launch)
-__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) { return __ldcg(p); }
-
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -194,53 +182,13 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-
-// ---- mbarrier and bulk copy (TMA, non-tensor) ----------------------------------------------
+// ---- asynchronous copies global -> shared ------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
 }
 
 // 16-byte asynchronous copy global -> shared (L2 only), tracked per thread
@@ -258,21 +206,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// arrive on the mbarrier once all of this thread's earlier cp.async copies have landed; the
-// arrival counts against the count the barrier was initialised with
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
 }
 
 }  // namespace cortex
@@ -296,7 +229,9 @@ cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* w
 cudaError_t launch_init_state(const NetDev* net_host, const NetDev* net_dev, int net_idx, float* V, float* I,
                               int32_t* R, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, cudaStream_t s);
-cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s);
+// apw: optional access-policy window of the launch (the ring kept resident in L2), NULL for none
+cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s,
+                        const cudaAccessPolicyWindow* apw = nullptr);
 cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s);
 // dynamic shared memory of a block of a network: nt targets per block (its largest block),
 // ring depth, window steps, nb blocks, staging bytes
@@ -304,6 +239,7 @@ size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, in
 void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m);
 cudaError_t step_kernel_attributes(size_t smem);
 int step_occupancy(int threads, size_t smem, bool ring_smem);
+
 cudaError_t launch_export(const NetDev* nets_dev, const BlockWork* work_dev, int block, int n_dw, const void* rec_w,
                           int wdtype, const uint16_t* rec_meta, const uint4* hdr, const unsigned long long* row_base,
                           int32_t n_src, int32_t t_begin, int32_t t_end, unsigned long long* counter, int32_t* src,

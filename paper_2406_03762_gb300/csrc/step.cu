@@ -173,6 +173,21 @@ __device__ __forceinline__ void ring_add(float* ring, uint32_t key, float w, boo
   }
 }
 
+// One ring cell += w when the build has shown that every partial sum of a cell is exact (every
+// weight an integer multiple of 2^e, e >= -126, and the sum of |w| / 2^e over a target's in-degree
+// below 2^24): the FP32 adds then round nothing, so any order gives the bits of the ordered fold,
+// and lanes that share a cell need no ordering.  Shared ring: a shared-memory reduction; global
+// ring: an L2 reduction.  Both flush subnormals, and none occurs (every nonzero partial sum is at
+// least 2^e >= 2^-126 in magnitude).
+template <bool kRingSmem>
+__device__ __forceinline__ void ring_add_exact(float* ring, uint32_t key, float w) {
+  if constexpr (kRingSmem) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_addr(ring + key)), "f"(w) : "memory");
+  } else {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(ring + key), "f"(w) : "memory");
+  }
+}
+
 // a ring cell read by the update: a global ring bypasses L1 (reductions are performed in L2)
 template <bool kRingSmem>
 __device__ __forceinline__ float ring_read(const float* p) {
@@ -223,30 +238,19 @@ __device__ __forceinline__ void fold_apply(float* ring, uint32_t key, float w, u
   }
 }
 
-// Fold G consecutive chunks: the sharing of all G is found first (each chunk writes its lane ids
-// into its own tag array and reads them back), then the ring updates run chunk after chunk.
-// Shared ring: one tag per cell (warps own disjoint cells).  Global ring: hashed tag arrays of
-// kTagHash bytes per warp.  The kernel folds one chunk per group (G = 1).
-template <bool kRingSmem, int G>
-__device__ __forceinline__ void fold_group(float* ring, uint8_t* wtags, const uint32_t* key, const float* w, int lane,
-                                           bool red) {
-  uint8_t* tg[G];
-#pragma unroll
-  for (int u = 0; u < G; ++u) {
-    const bool valid = key[u] != 0xffffffffu;
-    tg[u] = kRingSmem ? wtags + (valid ? key[u] : 0u) : wtags + u * kTagHash + (key[u] & (uint32_t)(kTagHash - 1));
-    if (valid) *tg[u] = (uint8_t)lane;
-  }
+// Fold one chunk: every lane writes its lane id into the tag of its cell and reads it back, which
+// finds the lanes that share a cell (shared ring: one tag per cell, since warps own disjoint cells;
+// global ring: a hashed tag array of kTagHash bytes per warp), then the ring updates run in lane
+// order.
+template <bool kRingSmem>
+__device__ __forceinline__ void fold_one(float* ring, uint8_t* wtags, uint32_t key, float w, int lane, bool red) {
+  const bool valid = key != 0xffffffffu;
+  uint8_t* tg = kRingSmem ? wtags + (valid ? key : 0u) : wtags + (key & (uint32_t)(kTagHash - 1));
+  if (valid) *tg = (uint8_t)lane;
   __syncwarp();
-  uint32_t t[G], losers[G];
-#pragma unroll
-  for (int u = 0; u < G; ++u) {
-    const bool valid = key[u] != 0xffffffffu;
-    t[u] = valid ? (uint32_t)*tg[u] : (uint32_t)lane;
-    losers[u] = __ballot_sync(0xffffffffu, valid && t[u] != (uint32_t)lane);
-  }
-#pragma unroll
-  for (int u = 0; u < G; ++u) fold_apply<kRingSmem>(ring, key[u], w[u], t[u], losers[u], lane, red);
+  const uint32_t t = valid ? (uint32_t)*tg : (uint32_t)lane;
+  const uint32_t losers = __ballot_sync(0xffffffffu, valid && t != (uint32_t)lane);
+  fold_apply<kRingSmem>(ring, key, w, t, losers, lane, red);
 }
 
 // Fold four consecutive chunks with one tag array, software-pipelined: chunk u + 1 writes its
@@ -283,8 +287,9 @@ __device__ __forceinline__ void fold_four(float* ring, uint8_t* wtags, const uin
 // phases: kPhaseUpdate, kPhaseDeliver, and kPhaseBarrier for the persistent form (both phases and
 // a barrier per window inside one cooperative launch of n_steps steps).  kRingSmem: the block's
 // ring slice lives in shared memory for the whole launch (loaded in the prologue, written back
-// in the epilogue); otherwise it is updated in place in global memory.
-template <bool kRingSmem, bool kBf16, bool kWide>
+// in the epilogue); otherwise it is updated in place in global memory.  kExact: the adds of the
+// delivery need no order (ring_add_exact), so the fold skips the sharing test.
+template <bool kRingSmem, bool kBf16, bool kWide, bool kExact>
 __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_step(const StepArgs a) {
   constexpr uint32_t kWsz = kBf16 ? 2u : 4u;  // bytes per stored weight
   // neuron chunks per update iteration: a global ring is read from L2, so several reads are kept
@@ -935,12 +940,22 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
             float wv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
-            fold_four<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
+            if constexpr (kExact) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (key[u] != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key[u], wv[u]);
+            } else {
+              fold_four<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
+            }
           }
           for (; e < total; e += 32) {
             float wv;
             const uint32_t key = chunk_key(e, wv);
-            fold_group<kRingSmem, 1>(ring, wtags, &key, &wv, lane, ring_red);
+            if constexpr (kExact) {
+              if (key != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key, wv);
+            } else {
+              fold_one<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
+            }
           }
         }
         __syncthreads();
@@ -994,36 +1009,48 @@ __global__ void k_advance(const StepArgs a, int n_nets, int wn) {
   if (net == 0) *a.step_counter += wn;
 }
 
-// the kernel variant for a launch: ring placement, weight type, and whether the block is wider
-// than kNarrowWarps warps
+// the kernel variant for a launch: ring placement, weight type, whether the block is wider than
+// kNarrowWarps warps, and whether the adds need an order
 using StepKernel = void (*)(StepArgs);
-StepKernel step_kernel(bool ring_smem, bool bf16, int threads) {
+template <bool kRingSmem, bool kBf16, bool kWide>
+StepKernel step_kernel_x(bool exact) {
+  return exact ? k_step<kRingSmem, kBf16, kWide, true> : k_step<kRingSmem, kBf16, kWide, false>;
+}
+template <bool kRingSmem, bool kBf16>
+StepKernel step_kernel_w(bool wide, bool exact) {
+  return wide ? step_kernel_x<kRingSmem, kBf16, true>(exact) : step_kernel_x<kRingSmem, kBf16, false>(exact);
+}
+StepKernel step_kernel(bool ring_smem, bool bf16, int threads, bool exact) {
   const bool wide = threads > kNarrowWarps * 32;
-  if (wide)
-    return ring_smem ? (bf16 ? k_step<true, true, true> : k_step<true, false, true>)
-                     : (bf16 ? k_step<false, true, true> : k_step<false, false, true>);
-  return ring_smem ? (bf16 ? k_step<true, true, false> : k_step<true, false, false>)
-                   : (bf16 ? k_step<false, true, false> : k_step<false, false, false>);
+  if (ring_smem) return bf16 ? step_kernel_w<true, true>(wide, exact) : step_kernel_w<true, false>(wide, exact);
+  return bf16 ? step_kernel_w<false, true>(wide, exact) : step_kernel_w<false, false>(wide, exact);
 }
 
-cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s) {
-  StepKernel kern = step_kernel(a.ring_smem != 0, a.bf16 != 0, threads);
+cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s,
+                        const cudaAccessPolicyWindow* apw) {
+  StepKernel kern = step_kernel(a.ring_smem != 0, a.bf16 != 0, threads, a.exact != 0);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
   if (cooperative) {
     // all blocks must be co-resident: they wait on each other at the window barrier
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
   }
-  kern<<<grid, threads, smem, s>>>(a);
-  return cudaGetLastError();
+  if (apw != nullptr && apw->num_bytes > 0) {
+    // the global ring is marked persisting in L2, so the streamed records do not evict it
+    attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[na].val.accessPolicyWindow = *apw;
+    ++na;
+  }
+  cfg.attrs = na ? attr : nullptr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s) {
@@ -1042,10 +1069,8 @@ void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m) {
 }
 
 cudaError_t step_kernel_attributes(size_t smem) {
-  const StepKernel kerns[8] = {k_step<true, false, false>, k_step<true, true, false>, k_step<false, false, false>,
-                               k_step<false, true, false>,  k_step<true, false, true>, k_step<true, true, true>,
-                               k_step<false, false, true>,  k_step<false, true, true>};
-  for (auto k : kerns) {
+  for (int v = 0; v < 16; ++v) {
+    const StepKernel k = step_kernel((v & 1) != 0, (v & 2) != 0, (v & 4) ? kMaxWarps * 32 : 32, (v & 8) != 0);
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -1055,7 +1080,7 @@ cudaError_t step_kernel_attributes(size_t smem) {
 int step_occupancy(int threads, size_t smem, bool ring_smem) {
   int n = 0;
   const cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel(ring_smem, false, threads), threads, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel(ring_smem, false, threads, false), threads, smem);
   return e == cudaSuccess ? n : 0;
 }
 

@@ -148,18 +148,65 @@ def test_simulate_in_pieces_equals_one_call(cortex):
             assert np.array_equal(x, y)
 
 
-def test_bf16_weights_match_oracle_with_bf16_weights(cortex):
+@pytest.mark.parametrize("opts", [dict(), dict(fold=1), dict(ring=2), dict(ring=2, fold=1, l2_persist=-1),
+                                  dict(mode=1, ring=2)])
+def test_bf16_weights_match_oracle_with_bf16_weights(cortex, opts):
     """BF16 storage with FP32 accumulation is deterministic: equal to the FP32 oracle run with the
-    weights rounded to bfloat16 (J_E 87.8 -> 88, J_I -439 -> -440)."""
+    weights rounded to bfloat16 (J_E 87.8 -> 88, J_I -439 -> -440).  These weights are multiples of
+    8 with K_E 88 + K_I 440 far below 2^24 * 8, so the build proves every partial sum exact and
+    folds without ordering (unless fold=1 asks for the ordered fold); both give the oracle's bits."""
     spec, seed, steps = SPECS[2], 99, 1500
-    with cortex.Network(spec, seed) as net:
+    with cortex.Network(spec, seed, cortex.make_options(**opts)) as net:
         net.simulate(steps)
         gs, gi = net.spikes()
+        gv, gc, gr = net.state()
         c6, _, _ = net.constants()
+        st = net.stats()
     assert c6[3] == 88.0 and c6[4] == -440.0
+    assert st["exact_fold"] == (0 if opts.get("fold") == 1 else 1)
+    if st["ring_in_smem"] == 0 and opts.get("l2_persist", 0) >= 0:
+        assert st["l2_persist_bytes"] > 0
     ref, os_, oi, _ = oracle_run(spec, seed, steps)
     assert len(os_) > 100
     assert first_mismatch(gs, gi, os_, oi) == -1
+    ov, oc, orr = ref.state()
+    assert np.array_equal(gv.astype(np.float64), ov) and np.array_equal(gc.astype(np.float64), oc)
+    assert np.array_equal(gr, orr)
+
+
+def test_exact_fold_is_refused_when_sums_can_round(cortex):
+    """FP32 weights 87.8 / -439 (87.8f has 23 significant bits): partial sums of a cell round, so
+    the order-free fold is not proven and fold=2 is refused; the default keeps the ordered fold."""
+    spec, seed = C0["spec"], C0["seed"]
+    with pytest.raises(cortex.CortexError) as e:
+        cortex.Network(spec, seed, cortex.make_options(fold=2))
+    assert e.value.code == cortex.ERR_UNSUPPORTED
+    with cortex.Network(spec, seed) as net:
+        assert net.stats()["exact_fold"] == 0
+
+
+def test_restore_of_a_ring_off_the_weight_grid_keeps_results(cortex):
+    """A restored ring whose values are not sums of the network's weights (here 0.1 pA) cannot use
+    the order-free fold: the handle returns to the ordered fold and still equals the oracle
+    started from the same state."""
+    spec, seed = SPECS[2], 99
+    ref = orc.Network(oracle_params(spec), seed)
+    ref.simulate(100)
+    v, c, r = ref.state()
+    ring = ref.ring().T.copy()
+    ring[3, 7] += np.float32(0.1)
+    ref.set_ring(ring.T)
+    ref.simulate(300)
+    s_all, i_all = ref.raster()
+    keep = s_all >= 100
+    with cortex.Network(spec, seed) as net:
+        assert net.stats()["exact_fold"] == 1
+        net.set_state(0, v=v.astype(np.float32), i_syn=c.astype(np.float32), refr=r, ring=ring.astype(np.float32))
+        assert net.stats()["exact_fold"] == 0
+        net.set_step(100)
+        net.simulate(300)
+        gs, gi = net.spikes()
+    assert first_mismatch(gs, gi, s_all[keep], i_all[keep]) == -1
 
 
 def test_batch_every_instance_matches_oracle(cortex):
