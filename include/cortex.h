@@ -59,6 +59,21 @@ extern "C" {
 #define CORTEX_FOLD_ORDERED 1        /* lanes sharing a cell add in stream order (always valid) */
 #define CORTEX_FOLD_EXACT 2          /* order-free adds; the build fails (UNSUPPORTED) unless proven */
 
+/* delivery schemes (cortex_options.delivery) */
+#define CORTEX_DELIVERY_RING 0       /* a spike's synapses are read at emission and added into a ring
+                                        of future input, D = d_max + 1 slots per neuron */
+#define CORTEX_DELIVERY_DELAY 1      /* delay-ordered (Sec. III-B "Varied Synaptic Delays", Sec. III-C
+                                        spike buffer): rows sorted by (delay, block, target); the
+                                        synapses of delay d of a spike at step e are read at step
+                                        e + d into an accumulator of that step (d_min + 1 per neuron,
+                                        in shared memory); the spikes of the last d_max steps are
+                                        kept in a spike buffer.  Same results as RING, bit for bit.
+                                        Persistent mode only; no ring to export or restore
+                                        (cortex_get_ring, cortex_set_state, cortex_set_step and
+                                        cortex_deliver return CORTEX_ERR_UNSUPPORTED).  Needs
+                                        (d_max - d_min + 1) * blocks <= 8192 and (d_max + 1) *
+                                        (blocks + 2) <= 6400 for a network's blocks. */
+
 /* step-loop modes (cortex_options.mode) */
 #define CORTEX_MODE_PERSISTENT 0     /* one cooperative kernel per chunk, grid barrier inside */
 #define CORTEX_MODE_SPLIT 1          /* an update kernel and a delivery kernel per window */
@@ -105,6 +120,7 @@ typedef struct cortex_options {
                                         persisting-L2 limit (cudaLimitPersistingL2CacheSize) to the
                                         ring's size, at most the device maximum; the previous limit
                                         is restored when the last handle that raised it is freed */
+  int32_t delivery;                  /* CORTEX_DELIVERY_* */
 } cortex_options;
 
 typedef struct cortex_stats_t {
@@ -128,6 +144,7 @@ typedef struct cortex_stats_t {
                                         (the largest network layout of a batch) */
   int32_t exact_fold;                /* 1 if the delivery uses order-free adds (CORTEX_FOLD_EXACT) */
   int64_t l2_persist_bytes;          /* bytes of the ring in the persisting L2 window (0: none) */
+  int32_t delivery;                  /* CORTEX_DELIVERY_* in use */
 } cortex_stats_t;
 
 typedef struct cortex_net cortex_net;

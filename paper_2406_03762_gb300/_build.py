@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcortex.so")
-SOURCES = ["build.cu", "step.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["build.cu", "step.cu", "step_delay.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]
@@ -29,7 +29,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in SOURCES]
-    files += [os.path.join(CSRC, "cortex_internal.cuh"), os.path.join(ROOT, "include", "cortex.h")]
+    files += [os.path.join(CSRC, h) for h in ("cortex_internal.cuh", "step_common.cuh")]
+    files += [os.path.join(ROOT, "include", "cortex.h")]
     return files
 
 

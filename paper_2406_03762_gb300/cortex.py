@@ -18,6 +18,7 @@ F32, BF16 = 0, 1
 RING_AUTO, RING_SMEM, RING_GLOBAL = 0, 1, 2
 MODE_PERSISTENT, MODE_SPLIT = 0, 1
 FOLD_AUTO, FOLD_ORDERED, FOLD_EXACT = 0, 1, 2
+DELIVERY_RING, DELIVERY_DELAY = 0, 1
 
 
 class CortexError(RuntimeError):
@@ -45,7 +46,7 @@ class Options(ctypes.Structure):
         ("raster_capacity", ctypes.c_int64), ("barrier_timeout_ms", ctypes.c_double),
         ("spikes_per_round", ctypes.c_int32), ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
         ("net_work", ctypes.POINTER(ctypes.c_float)),
-        ("fold", ctypes.c_int32), ("l2_persist", ctypes.c_int32),
+        ("fold", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("delivery", ctypes.c_int32),
     ]
 
     def work(self):
@@ -62,7 +63,7 @@ class Stats(ctypes.Structure):
         ("simulate_events", ctypes.c_int64), ("n_blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
         ("ring_in_smem", ctypes.c_int32), ("mode", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
         ("spikes_per_round", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
-        ("exact_fold", ctypes.c_int32), ("l2_persist_bytes", ctypes.c_int64),
+        ("exact_fold", ctypes.c_int32), ("l2_persist_bytes", ctypes.c_int64), ("delivery", ctypes.c_int32),
     ]
 
     def as_dict(self):

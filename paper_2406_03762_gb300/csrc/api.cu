@@ -82,6 +82,18 @@ struct cortex_net {
   int e_min = 0;          // exact: every weight is an integer multiple of 2^e_min
   double exact_bound = 0; // exact: largest |partial sum| of a cell, in units of 2^e_min
   cudaAccessPolicyWindow apw = {};  // the global ring, persisting in L2 (num_bytes 0: none)
+  // delay-ordered delivery
+  int delivery = CORTEX_DELIVERY_RING;
+  int d_threads = 1024;   // threads per block of the delay-ordered kernel
+  size_t d_smem = 0;      // its dynamic shared memory
+  uint16_t* dtgt = nullptr;
+  void* dw = nullptr;
+  uint16_t* dtbl = nullptr;
+  uint32_t* hist_ids = nullptr;
+  uint32_t* hist_cnt = nullptr;
+  unsigned long long* bar_count = nullptr;
+  int hist_max = 0;
+  int64_t total_tbl = 0;
   bool l2_user = false;   // this handle raised the process's persisting-L2 limit
   int mode = CORTEX_MODE_PERSISTENT;
   int stage_bytes = 0, batch = 32;  // largest staging area, fewest spikes per round (stats)
@@ -359,7 +371,7 @@ int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_optio
     if (params[b].weight_dtype != params[0].weight_dtype)
       return fail(CORTEX_ERR_UNSUPPORTED, "all networks of a batch must use the same weight_dtype");
   }
-  if (o.warps_per_block < 0 || o.warps_per_block > kMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..16");
+  if (o.warps_per_block < 0) return fail(CORTEX_ERR_ARG, "warps_per_block must be >= 0");
   if (o.mode != CORTEX_MODE_PERSISTENT && o.mode != CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_ARG, "mode");
   if (o.ring < 0 || o.ring > 2) return fail(CORTEX_ERR_ARG, "ring");
   if (o.balance < 0 || o.balance > 2) return fail(CORTEX_ERR_ARG, "balance");
@@ -371,6 +383,13 @@ int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_optio
   if (o.spikes_per_round < 0 || o.spikes_per_round > kSpikeBatch) return fail(CORTEX_ERR_ARG, "spikes_per_round must be 0..32");
   if (o.fold < CORTEX_FOLD_AUTO || o.fold > CORTEX_FOLD_EXACT) return fail(CORTEX_ERR_ARG, "fold must be 0..2");
   if (o.l2_persist < -1 || o.l2_persist > 1) return fail(CORTEX_ERR_ARG, "l2_persist must be -1, 0 or 1");
+  if (o.delivery != CORTEX_DELIVERY_RING && o.delivery != CORTEX_DELIVERY_DELAY) return fail(CORTEX_ERR_ARG, "delivery");
+  if (o.delivery == CORTEX_DELIVERY_DELAY) {
+    if (o.mode == CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery runs in persistent mode only");
+    if (o.warps_per_block < 0 || o.warps_per_block > kDMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..32");
+  } else if (o.warps_per_block > kMaxWarps) {
+    return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..16");
+  }
   return CORTEX_OK;
 }
 
@@ -429,6 +448,13 @@ StepArgs make_args(cortex_net* h) {
   a.bf16 = h->wdtype == CORTEX_BF16 ? 1 : 0;
   a.withhold_block = h->withhold_block;
   a.t_fixed = -1;
+  a.dtgt = h->dtgt;
+  a.dw = h->dw;
+  a.dtbl = h->dtbl;
+  a.hist_ids = h->hist_ids;
+  a.hist_cnt = h->hist_cnt;
+  a.hist_max = h->hist_max;
+  a.bar_count = h->bar_count;
   return a;
 }
 
@@ -437,6 +463,7 @@ cudaError_t launch_persistent(cortex_net* h, int n_steps, cudaStream_t s) {
   a.n_steps = n_steps;
   a.phases = kPhaseUpdate | kPhaseDeliver | kPhaseBarrier;
   a.ring_smem = h->ring_smem ? 1 : 0;
+  if (h->delivery == CORTEX_DELIVERY_DELAY) return launch_dstep(a, h->n_blocks, h->d_threads, h->d_smem, s);
   return launch_step(a, h->n_blocks, h->threads, h->smem, true, s, &h->apw);
 }
 
@@ -649,7 +676,15 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   h->params.assign(params, params + n_nets);
   h->seeds.assign(seeds, seeds + n_nets);
   h->wdtype = params[0].weight_dtype;
-  h->n_warps = o.warps_per_block ? o.warps_per_block : 14;
+  h->delivery = o.delivery;
+  if (h->delivery == CORTEX_DELIVERY_DELAY) {
+    // the delay-ordered kernel runs up to 32 warps; the records are first built in the ring layout,
+    // whose piece headers describe at most 16 warps
+    h->d_threads = 32 * (o.warps_per_block ? o.warps_per_block : kDMaxWarps);
+    h->n_warps = std::min(o.warps_per_block ? o.warps_per_block : 14, kMaxWarps);
+  } else {
+    h->n_warps = o.warps_per_block ? o.warps_per_block : 14;
+  }
   h->threads = 32 * h->n_warps;
   h->mode = o.mode;
   h->steps_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 1000;
@@ -706,6 +741,19 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     d.raster_base = raster;
     d.raster_cap = rcap;
     raster += rcap;
+    d.tbl_stride = (p.d_max - p.d_min + 1) * nbk + 1;
+    d.tbl_base = h->total_tbl;
+    d.hist_depth = p.d_max + d.window + 1;
+    if (h->delivery == CORTEX_DELIVERY_DELAY) {
+      if ((p.d_max - p.d_min + 1) * nbk > kDLayCap)
+        return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: (d_max - d_min + 1) * blocks of a network above " +
+                                                     std::to_string(kDLayCap)));
+      if ((p.d_max + 1) * (nbk + 2) > kDCntCap)
+        return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: (d_max + 1) * (blocks + 2) of a network above " +
+                                                     std::to_string(kDCntCap)));
+      h->total_tbl += (int64_t)d.n * d.tbl_stride;
+      h->hist_max = std::max(h->hist_max, d.hist_depth);
+    }
     const int32_t tw = (int32_t)ceil_div(tb[b], h->n_warps);  // targets per warp
     if ((int64_t)tw > (1ll << (16 - d.dbits)))
       return bail(fail(CORTEX_ERR_UNSUPPORTED, "targets per delivery warp (" + std::to_string(tw) +
@@ -777,6 +825,14 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(h->alloc(&h->err, 16), "alloc err");
   TRY(h->alloc(&h->step_counter, 16), "alloc step");
   TRY(h->alloc(&h->max_seg, 4 * (size_t)n_nets), "alloc max_seg");
+  if (h->delivery == CORTEX_DELIVERY_DELAY) {
+    TRY(h->alloc(&h->dtgt, 2 * h->total_syn + 64), "alloc delay-ordered targets");
+    TRY(h->alloc(&h->dw, wsz * h->total_syn + 64), "alloc delay-ordered weights");
+    TRY(h->alloc(&h->dtbl, 2 * h->total_tbl + 64), "alloc delay tables");
+    TRY(h->alloc(&h->hist_ids, 4 * (size_t)h->hist_max * h->n_total), "alloc spike buffer");
+    TRY(h->alloc(&h->hist_cnt, 4 * (size_t)h->hist_max * h->n_blocks), "alloc spike buffer counts");
+    TRY(h->alloc(&h->bar_count, 8 * (size_t)n_nets), "alloc barrier counters");
+  }
 
   TRY(cudaEventRecord(h->ev0, s), "event");
   TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * n_nets, cudaMemcpyHostToDevice, s), "upload nets");
@@ -794,6 +850,14 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     rc = build_network(h, b, tb);
     if (rc != CORTEX_OK) return bail(rc);
     TRY(launch_init_state(&h->nets_h[b], h->nets_d, b, h->V, h->I, h->R, s), "init state");
+    if (h->delivery == CORTEX_DELIVERY_DELAY)
+      TRY(launch_delay_layout(h->nets_d, &h->nets_h[b], h->work_d, b, h->n_warps, h->hdr, h->row_base, h->rec_w,
+                              h->rec_meta, h->dtbl, h->dtgt, h->dw, h->err, s),
+          "delay-ordered layout");
+  }
+  if (h->delivery == CORTEX_DELIVERY_DELAY) {
+    TRY(cudaMemsetAsync(h->hist_cnt, 0, 4 * (size_t)h->hist_max * h->n_blocks, s), "memset spike buffer");
+    TRY(cudaMemsetAsync(h->bar_count, 0, 8 * (size_t)n_nets, s), "memset barrier");
   }
   TRY(cudaMemsetAsync(h->ring, 0, 4 * h->total_ring, s), "memset ring");
   TRY(cudaMemsetAsync(h->pub_flag, 0, 8 * (size_t)h->n_blocks, s), "memset flags");
@@ -812,7 +876,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
 
   rc = choose_stage_and_ring(h, o);
   if (rc != CORTEX_OK) return bail(rc);
-  if (h->mode == CORTEX_MODE_PERSISTENT) {
+  if (h->mode == CORTEX_MODE_PERSISTENT && h->delivery == CORTEX_DELIVERY_RING) {
     const int occ = step_occupancy(h->threads, h->smem, h->ring_smem);
     if (occ * h->n_sm < h->n_blocks) {
       if (o.mode == CORTEX_MODE_PERSISTENT && opts && opts->mode == CORTEX_MODE_PERSISTENT && o.ring == CORTEX_RING_SMEM)
@@ -829,7 +893,22 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
       return bail(fail(CORTEX_ERR_UNSUPPORTED, "fold EXACT: the weights do not make every partial sum of a ring cell exact"));
     h->exact = proven && o.fold != CORTEX_FOLD_ORDERED;
   }
-  if (!h->ring_smem && o.l2_persist >= 0) l2_persist_acquire(h, 4 * h->total_ring);
+  if (h->delivery == CORTEX_DELIVERY_DELAY) {
+    if (h->mode != CORTEX_MODE_PERSISTENT)
+      return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: the blocks cannot all be resident"));
+    h->d_smem = 0;
+    for (const NetDev& d : h->nets_h)
+      h->d_smem = std::max(h->d_smem, dstep_smem_bytes(h->work_h[d.first_block].nt, d.window, d.n_blocks,
+                                                       h->d_threads / 32, h->exact));
+    if (h->d_smem > h->smem_cap)
+      return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: the accumulators and state of a block need " +
+                                                   std::to_string(h->d_smem) + " bytes of shared memory"));
+    TRY(dstep_kernel_attributes(h->d_smem), "delay kernel attributes");
+    if (dstep_occupancy(h->d_threads, h->d_smem) * h->n_sm < h->n_blocks)
+      return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: the blocks cannot all be resident"));
+  } else if (!h->ring_smem && o.l2_persist >= 0) {
+    l2_persist_acquire(h, 4 * h->total_ring);
+  }
 #undef TRY
   *out = h;
   return CORTEX_OK;
@@ -1050,6 +1129,12 @@ int cortex_stats(cortex_net* h, cortex_stats_t* st) {
   st->smem_bytes = (int32_t)h->smem;
   st->exact_fold = h->exact ? 1 : 0;
   st->l2_persist_bytes = (int64_t)h->apw.num_bytes;
+  st->delivery = h->delivery;
+  if (h->delivery == CORTEX_DELIVERY_DELAY) {
+    st->threads_per_block = h->d_threads;
+    st->smem_bytes = (int32_t)h->d_smem;
+    st->ring_in_smem = 0;
+  }
   return CORTEX_OK;
 }
 
@@ -1065,6 +1150,8 @@ int cortex_get_state(cortex_net* h, int32_t net_idx, float* v, float* i_syn, int
 
 int cortex_get_ring(cortex_net* h, int32_t net_idx, float* ring) {
   if (!h || !ring || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_get_ring: arguments");
+  if (h->delivery == CORTEX_DELIVERY_DELAY)
+    return fail(CORTEX_ERR_UNSUPPORTED, "cortex_get_ring: delay-ordered delivery keeps a spike buffer, not a ring");
   const NetDev& d = h->nets_h[net_idx];
   // each block holds [D][T_b] floats of its targets; the host array is [D][n]
   for (int g = 0; g < d.n_blocks; ++g) {
@@ -1079,6 +1166,8 @@ int cortex_get_ring(cortex_net* h, int32_t net_idx, float* ring) {
 int cortex_set_state(cortex_net* h, int32_t net_idx, const float* v, const float* i_syn, const int32_t* refr,
                      const float* ring) {
   if (!h || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_set_state: arguments");
+  if (h->delivery == CORTEX_DELIVERY_DELAY)
+    return fail(CORTEX_ERR_UNSUPPORTED, "cortex_set_state: delay-ordered delivery keeps a spike buffer, not a ring");
   if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_set_state: an earlier device wait timed out; free the handle");
   const NetDev& d = h->nets_h[net_idx];
   if (refr)
@@ -1116,6 +1205,8 @@ int cortex_set_state(cortex_net* h, int32_t net_idx, const float* v, const float
 
 int cortex_set_step(cortex_net* h, int64_t step) {
   if (!h || step < 0) return fail(CORTEX_ERR_ARG, "cortex_set_step: arguments");
+  if (h->delivery == CORTEX_DELIVERY_DELAY)
+    return fail(CORTEX_ERR_UNSUPPORTED, "cortex_set_step: delay-ordered delivery keeps a spike buffer, not a ring");
   if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_set_step: an earlier device wait timed out; free the handle");
   const long long st = (long long)step;
   CUDA_TRY(cudaMemcpyAsync(h->step_counter, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
@@ -1205,6 +1296,8 @@ int cortex_deliver(cortex_net* h, int32_t net_idx, const int32_t* ids, int64_t n
                    double* ms_out, int64_t* events_out) {
   if (!h || net_idx < 0 || net_idx >= h->n_nets || n < 0 || (n > 0 && !ids) || t_emit < 0 || reps < 1)
     return fail(CORTEX_ERR_ARG, "cortex_deliver: arguments");
+  if (h->delivery == CORTEX_DELIVERY_DELAY)
+    return fail(CORTEX_ERR_UNSUPPORTED, "cortex_deliver: measures the ring delivery only");
   const NetDev& d = h->nets_h[net_idx];
   std::vector<int32_t> v(ids, ids + n);
   for (int32_t x : v)

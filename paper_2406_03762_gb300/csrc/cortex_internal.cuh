@@ -50,6 +50,13 @@ constexpr int kIdCap = 2048;        // spike ids of a window kept in shared memo
 constexpr int kMboxWords = 16;      // 64-bit words of a block's mailbox line (128 bytes)
 constexpr int kInlMax = 3 * (kMboxWords - 1);  // spike ids a mailbox line carries (one count word)
 
+// delay-ordered delivery: (emission step, block) spike counts and spike ids a block keeps in shared
+// memory while it folds a window
+constexpr int kDCntCap = 6400;
+constexpr int kDIdCap = 4096;
+constexpr int kDMaxWarps = 32;      // warps per block of the delay-ordered kernel
+constexpr int kDLayCap = 8192;      // (delay, block) pieces of one source the layout builder counts
+
 constexpr uint32_t kStreamConn = 1u;
 constexpr uint32_t kStreamV0 = 2u;
 constexpr uint32_t kStreamPoisson = 3u;
@@ -80,6 +87,10 @@ struct NetDev {
   int64_t hdr_base;                            // first header of this network (source-major)
   int64_t row_off;                             // offset of this network in row_base
   int64_t raster_base, raster_cap;             // offset and capacity in the raster arrays
+  // delay-ordered delivery (records sorted by source, delay, block, target, draw)
+  int64_t tbl_base;                            // first table word of this network
+  int32_t tbl_stride;                          // table words per source: n_delays * n_blocks + 1
+  int32_t hist_depth;                          // steps of spike history kept: d_max + window + 1
   uint32_t thr[kPoissonCap];
 };
 
@@ -130,6 +141,14 @@ struct StepArgs {
   int32_t withhold_block;             // test hook: this block never publishes (-1: none)
   // delivery-only launches (cortex_deliver): fixed emission step
   long long t_fixed;
+  // delay-ordered delivery
+  const uint16_t* dtgt;               // block-local target of every record (delay-ordered rows)
+  const void* dw;                     // weight of every record (f32 or bf16)
+  const uint16_t* dtbl;               // per source: offsets in its row of the (delay, block) pieces
+  uint32_t* hist_ids;                 // [hist slot][n_total]: ids a block emitted at a step
+  uint32_t* hist_cnt;                 // [hist slot][n_blocks]: how many
+  int32_t hist_max;                   // slots of the history arrays (largest hist_depth)
+  unsigned long long* bar_count;      // per network: window arrivals of its blocks (monotonic)
 };
 
 constexpr int kPhaseUpdate = 1;
@@ -182,6 +201,27 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// position of the n-th (0-based) set bit of m; m has more than n set bits
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(m & ((1u << s) - 1u));
+    if (n >= c) {
+      n -= c;
+      m >>= s;
+      pos += s;
+    }
+  }
+  return pos;
+}
+
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -229,6 +269,14 @@ cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* w
 cudaError_t launch_init_state(const NetDev* net_host, const NetDev* net_dev, int net_idx, float* V, float* I,
                               int32_t* R, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out, cudaStream_t s);
+cudaError_t launch_delay_layout(const NetDev* nets_dev, const NetDev* net_host, const BlockWork* work_dev, int net_idx,
+                                int n_dw, const uint4* hdr, const unsigned long long* row_base, const void* rec_w,
+                                const uint16_t* rec_meta, uint16_t* dtbl, uint16_t* dtgt, void* dw, int32_t* err,
+                                cudaStream_t s);
+cudaError_t launch_dstep(const StepArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
+size_t dstep_smem_bytes(int nt, int window, int nb, int n_warps, bool exact);
+cudaError_t dstep_kernel_attributes(size_t smem);
+int dstep_occupancy(int threads, size_t smem);
 // apw: optional access-policy window of the launch (the ring kept resident in L2), NULL for none
 cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, bool cooperative, cudaStream_t s,
                         const cudaAccessPolicyWindow* apw = nullptr);
