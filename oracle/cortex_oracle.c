@@ -1,5 +1,6 @@
 /*
- * cortex_oracle.c -- plain, slow, single-threaded CPU reference simulator.
+ * cortex_oracle.c -- plain, slow CPU reference simulator (single-threaded, or target-partitioned
+ * over threads with bitwise-identical results).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU-baseline leg of
  * the benchmark load this file.  The CUDA library never links or calls it, and it shares no
@@ -242,6 +243,13 @@ typedef struct oracle_net {
   int64_t* consumed_events;  /* optional [n] events consumed per target */
   double* consumed_weight;   /* optional [n] weight consumed per target (double sum) */
   double* weight_ring;       /* optional [n][D] double shadow of the ring for the above */
+  /* target-partitioned form (oracle_build_par): part k owns targets [part_lo[k], part_lo[k+1])
+   * and keeps its own CSR by source of their incoming synapses, sorted by (source, target, draw) */
+  int32_t n_part;            /* 0: the single lists above */
+  int64_t* part_lo;          /* [n_part + 1] */
+  int64_t** prow;            /* [n_part][n + 1] */
+  int32_t** ptgt;            /* [n_part][synapses of the part] */
+  uint8_t** pdly;
 } oracle_net;
 
 static void* xcalloc(size_t n, size_t sz) { return (n == 0) ? calloc(1, 1) : calloc(n, sz); }
@@ -320,6 +328,12 @@ void oracle_free(oracle_net* net) {
   free(net->refr); free(net->raster_step); free(net->raster_id);
   free(net->count_ring); free(net->consumed_events); free(net->consumed_weight);
   free(net->weight_ring);
+  for (int32_t k = 0; k < net->n_part; ++k) {
+    if (net->prow) free(net->prow[k]);
+    if (net->ptgt) free(net->ptgt[k]);
+    if (net->pdly) free(net->pdly[k]);
+  }
+  free(net->part_lo); free(net->prow); free(net->ptgt); free(net->pdly);
   free(net);
 }
 
@@ -519,11 +533,122 @@ static void deliver(oracle_net* net, int32_t s, int64_t t) {
   }
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Target-partitioned form (Sec. III-B "Avoid Data Racing": each thread owns a set of post-      */
+/* synaptic neurons and the synapses into them, so no two threads write the same ring cell).     */
+/* ------------------------------------------------------------------------------------------ */
+/* Part k builds the incoming synapses of its target range exactly as oracle_build does for all
+ * targets (ascending targets, ascending draws), so the part's list of a source is the global list
+ * of that source restricted to the part's targets, in the same (target, draw) order.  Every ring
+ * cell therefore receives the same adds in the same order as in the single-list form: the results
+ * are the same bits, whatever the number of parts. */
+int oracle_build_par(const oracle_params* p, uint64_t seed, int32_t n_part, oracle_net** out) {
+  *out = NULL;
+  if (!validate(p) || n_part < 1) return ORACLE_ERR_ARG;
+  oracle_net* net = (oracle_net*)calloc(1, sizeof(oracle_net));
+  if (!net) return ORACLE_ERR_OOM;
+  int rc = init_common(net, p, seed);
+  if (rc != ORACLE_OK) { oracle_free(net); return rc; }
+  const int64_t n = net->n, k = (int64_t)p->k_exc + p->k_inh;
+  if (n_part > n) n_part = (int32_t)n;
+  net->n_syn = n * k;
+  net->part_lo = (int64_t*)xcalloc((size_t)n_part + 1, sizeof(int64_t));
+  net->prow = (int64_t**)xcalloc((size_t)n_part, sizeof(int64_t*));
+  net->ptgt = (int32_t**)xcalloc((size_t)n_part, sizeof(int32_t*));
+  net->pdly = (uint8_t**)xcalloc((size_t)n_part, sizeof(uint8_t*));
+  if (!net->part_lo || !net->prow || !net->ptgt || !net->pdly) { oracle_free(net); return ORACLE_ERR_OOM; }
+  net->n_part = n_part;
+  for (int32_t q = 0; q <= n_part; ++q) net->part_lo[q] = n * q / n_part;
+  int failed = 0;
+#pragma omp parallel for num_threads(n_part) schedule(static, 1) reduction(| : failed)
+  for (int32_t q = 0; q < n_part; ++q) {
+    const int64_t lo = net->part_lo[q], hi = net->part_lo[q + 1];
+    int64_t* row = (int64_t*)xcalloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* cursor = (int64_t*)xcalloc((size_t)n + 1, sizeof(int64_t));
+    int32_t* tgt = (int32_t*)xcalloc((size_t)((hi - lo) * k), sizeof(int32_t));
+    uint8_t* dly = (uint8_t*)xcalloc((size_t)((hi - lo) * k), sizeof(uint8_t));
+    net->prow[q] = row; net->ptgt[q] = tgt; net->pdly[q] = dly;
+    if (!row || !cursor || !tgt || !dly) { free(cursor); failed |= 1; continue; }
+    int32_t s, d;
+    for (int64_t i = lo; i < hi; ++i)
+      for (int64_t j = 0; j < k; ++j) {
+        oracle_draw(seed, p->n_exc, p->n_inh, p->k_exc, p->d_min, p->d_max, i, j, &s, &d);
+        row[s + 1] += 1;
+      }
+    for (int64_t x = 0; x < n; ++x) row[x + 1] += row[x];
+    for (int64_t x = 0; x < n; ++x) cursor[x] = row[x];
+    for (int64_t i = lo; i < hi; ++i)
+      for (int64_t j = 0; j < k; ++j) {
+        oracle_draw(seed, p->n_exc, p->n_inh, p->k_exc, p->d_min, p->d_max, i, j, &s, &d);
+        int64_t pos = cursor[s]++;
+        tgt[pos] = (int32_t)i;
+        dly[pos] = (uint8_t)d;
+      }
+    free(cursor);
+  }
+  if (failed) { oracle_free(net); return ORACLE_ERR_OOM; }
+  *out = net;
+  return ORACLE_OK;
+}
+
+/* Deliver the spike of source s emitted at step t onto the targets of part q (its own list). */
+static void deliver_part(oracle_net* net, int32_t q, int32_t s, int64_t t) {
+  const int64_t* row = net->prow[q];
+  const int is_exc = s < net->p.n_exc;
+  for (int64_t e = row[s]; e < row[s + 1]; ++e) {
+    size_t cell = (size_t)net->ptgt[q][e] * (size_t)net->depth + (size_t)((t + net->pdly[q][e]) % net->depth);
+    if (net->p.precision == ORACLE_FP32) {
+      float w = is_exc ? net->wexf : net->winf;
+      net->ring32[cell] = net->ring32[cell] + w;
+    } else {
+      double w = is_exc ? net->p.j_exc : net->p.j_inh;
+      net->ring64[cell] = net->ring64[cell] + w;
+    }
+  }
+}
+
+/* The simulation loop of oracle_simulate with the target ranges stepped by their own threads:
+ * every part updates its neurons; the spikes are recorded in ascending id (one thread); every part
+ * delivers every spike, in ascending source order, onto its own targets. */
+static int simulate_par(oracle_net* net, int64_t n_steps) {
+  char* emitted = (char*)xcalloc((size_t)net->n, 1);
+  if (!emitted) return ORACLE_ERR_OOM;
+  int rc = ORACLE_OK;
+  const int32_t n_part = net->n_part;
+#pragma omp parallel num_threads(n_part)
+  {
+    for (int64_t step = 0; step < n_steps; ++step) {
+      const int64_t t = net->step + step;
+#pragma omp for schedule(static, 1)
+      for (int32_t q = 0; q < n_part; ++q)
+        for (int64_t i = net->part_lo[q]; i < net->part_lo[q + 1]; ++i)
+          emitted[i] = (char)((net->p.precision == ORACLE_FP32) ? step_neuron_f32(net, i, t) : step_neuron_f64(net, i, t));
+#pragma omp single
+      for (int64_t i = 0; i < net->n; ++i) {
+        if (!emitted[i]) continue;
+        if (push_spike(net, t, (int32_t)i) != ORACLE_OK) rc = ORACLE_ERR_OOM;
+        for (int32_t q = 0; q < n_part; ++q) net->events += net->prow[q][i + 1] - net->prow[q][i];
+      }
+#pragma omp for schedule(static, 1)
+      for (int32_t q = 0; q < n_part; ++q)
+        for (int64_t i = 0; i < net->n; ++i)
+          if (emitted[i]) deliver_part(net, q, (int32_t)i, t);
+    }
+  }
+  net->step += n_steps;
+  free(emitted);
+  return rc;
+}
+
 /* Advance n_steps from the current step.  Forced spikes (test hook, sorted by step) are emitted
  * in addition to the neurons' own spikes, without touching their state. */
 int oracle_simulate(oracle_net* net, int64_t n_steps, int64_t n_forced, const int64_t* forced_step,
                     const int32_t* forced_id, int64_t n_trace, const int32_t* trace_ids,
                     double* v_trace) {
+  if (net->n_part > 0) {
+    if (n_forced > 0 || n_trace > 0 || net->count_ring) return ORACLE_ERR_ARG;  /* single-list form only */
+    return simulate_par(net, n_steps);
+  }
   int64_t fq = 0;
   char* emitted = (char*)xcalloc((size_t)net->n, 1);
   if (!emitted) return ORACLE_ERR_OOM;

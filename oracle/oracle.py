@@ -37,9 +37,12 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
            "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    if subprocess.run(cmd, capture_output=True).returncode != 0:
+        # no OpenMP runtime: the target-partitioned form then runs its parts one after another
+        cmd.remove("-fopenmp")
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -89,6 +92,8 @@ def lib():
         L.oracle_build_edges.argtypes = [P(_Params), ctypes.c_uint64, ctypes.c_int64, P(ctypes.c_int32),
                                          P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double), P(vp)]
         L.oracle_build_edges.restype = ctypes.c_int
+        L.oracle_build_par.argtypes = [P(_Params), ctypes.c_uint64, ctypes.c_int32, P(vp)]
+        L.oracle_build_par.restype = ctypes.c_int
         L.oracle_free.argtypes = [vp]
         L.oracle_free.restype = None
         L.oracle_enable_accounting.argtypes = [vp]
@@ -265,12 +270,16 @@ def replay(p: Params, seed: int, targets, n_steps: int, raster_steps, raster_ids
 class Network:
     """One oracle network (Philox connectivity or a hand-built edge list)."""
 
-    def __init__(self, p: Params, seed: int, edges=None, accounting: bool = False):
+    def __init__(self, p: Params, seed: int, edges=None, accounting: bool = False, threads: int = 1):
+        """threads > 1: the target-partitioned form (same results bit for bit; no forced spikes,
+        traces or accounting)."""
         self.p = p
         self.seed = seed
         h = ctypes.c_void_p(None)
         cp = p.c()
-        if edges is None:
+        if edges is None and threads > 1:
+            rc = lib().oracle_build_par(ctypes.byref(cp), seed, int(threads), ctypes.byref(h))
+        elif edges is None:
             rc = lib().oracle_build(ctypes.byref(cp), seed, ctypes.byref(h))
         else:
             src, tgt, dly, w = (np.ascontiguousarray(edges[0], np.int32), np.ascontiguousarray(edges[1], np.int32),
