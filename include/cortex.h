@@ -156,7 +156,8 @@ typedef struct cortex_net cortex_net;
  * stream: cudaStream_t or NULL.  opts may be NULL.  On success *out owns all device memory.
  * Errors: CORTEX_ERR_ARG (invalid parameters), CORTEX_ERR_UNSUPPORTED (sizes beyond the
  * layout limits: in-degree or targets per block > 65535, d_max > 255, more than 2,048 synapses
- * from one source into one block, no block plan within the SMs and their shared memory),
+ * from one source into one block, a source's row (its out-degree) above 65,535 synapses, no block
+ * plan within the SMs and their shared memory),
  * CORTEX_ERR_OOM, CORTEX_ERR_CUDA.  On error *out is NULL and nothing is leaked. */
 int cortex_build(const cortex_params* params, uint64_t seed, const cortex_options* opts,
                  void* stream, cortex_net** out);
@@ -280,10 +281,12 @@ int cortex_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t*
  * weight as stored: bfloat16-rounded when weight_dtype is CORTEX_BF16).  Work is issued on stream
  * and the call synchronises it.
  * Working memory is one static 8 MiB device array per GPU: (n + 1) + (t_end - t_begin) * K must be
- * at most 2^21 words, t_end - t_begin at most 65536, and no source may have more than 2048
- * synapses in the range; larger sizes return CORTEX_ERR_UNSUPPORTED without launching anything.
- * The first call on a device looks up the array's device address (with that device current);
- * make that first call before any stream capture.  Every call reuses the same array (it is cleared
+ * at most 2^21 words and t_end - t_begin at most 65536; larger sizes return CORTEX_ERR_UNSUPPORTED
+ * without launching anything.  No source may have more than 2048 synapses in the range: that is
+ * found on the device, after the outputs were partly written, and returns CORTEX_ERR_UNSUPPORTED
+ * with the outputs undefined.  Every call copies a status word to pageable host memory and
+ * synchronises the stream, so a call cannot be captured in a CUDA graph.  The first call on a
+ * device looks up the array's device address (with that device current).  Every call reuses the same array (it is cleared
  * at the start of each call), so calls that overlap on the GPU -- on different streams or host
  * threads -- race and must be serialised by the caller.  Errors: CORTEX_ERR_ARG (bad parameters
  * or NULL outputs), CORTEX_ERR_UNSUPPORTED (size limits), CORTEX_ERR_CUDA. */

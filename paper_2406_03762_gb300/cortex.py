@@ -356,9 +356,39 @@ def philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
     return out
 
 
+def _check_device_buffer(name: str, t, dtype: str, min_numel: int):
+    """A caller-owned output of cortex_subgraph_noalloc: the C side cannot see the size or the type
+    of a device buffer, so a wrong one is refused here, before any launch (CortexError ERR_ARG)."""
+    if t is None:
+        if min_numel > 0:
+            raise CortexError(ERR_ARG, "cortex_subgraph_noalloc", f"{name} is None")
+        return
+    if not getattr(t, "is_cuda", False):
+        raise CortexError(ERR_ARG, "cortex_subgraph_noalloc", f"{name} must be a CUDA tensor")
+    if str(getattr(t, "dtype", "")).replace("torch.", "") != dtype:
+        raise CortexError(ERR_ARG, "cortex_subgraph_noalloc", f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise CortexError(ERR_ARG, "cortex_subgraph_noalloc", f"{name} must be contiguous")
+    if t.numel() < min_numel:
+        raise CortexError(ERR_ARG, "cortex_subgraph_noalloc", f"{name} holds {t.numel()} elements, needs {min_numel}")
+    dev = getattr(t, "device", None)
+    idx = getattr(dev, "index", None)
+    if idx is not None:
+        import torch
+        if idx != torch.cuda.current_device():
+            raise CortexError(ERR_ARG, "cortex_subgraph_noalloc", f"{name} is on cuda:{idx}, not the current device")
+
+
 def subgraph_noalloc(spec, seed: int, t_begin: int, t_end: int, row_ptr, tgt, delay, weight, stream=None):
-    """cortex_subgraph_noalloc: the caller passes device buffers (anything with data_ptr(), e.g.
-    torch CUDA tensors: int32 row_ptr[n + 1], int32 tgt/delay[nnz], float32 weight[nnz])."""
+    """cortex_subgraph_noalloc: the caller passes contiguous CUDA tensors on the current device:
+    int32 row_ptr[n + 1], int32 tgt/delay[nnz], float32 weight[nnz], nnz = (t_end - t_begin) * K.
+    Each is checked (type, device, size) before the call, since the library writes into them."""
+    n, k = spec.n_exc + spec.n_inh, spec.k_exc + spec.k_inh
+    nnz = max(0, int(t_end) - int(t_begin)) * k
+    _check_device_buffer("row_ptr", row_ptr, "int32", n + 1)
+    _check_device_buffer("tgt", tgt, "int32", nnz)
+    _check_device_buffer("delay", delay, "int32", nnz)
+    _check_device_buffer("weight", weight, "float32", nnz)
     p = params_from_spec(spec)
     ptr = lambda t: ctypes.c_void_p(int(t.data_ptr())) if t is not None else None
     _check(load().cortex_subgraph_noalloc(ctypes.byref(p), int(seed), int(t_begin), int(t_end), _stream_handle(stream),

@@ -21,10 +21,7 @@ namespace {
 
 thread_local std::string g_last_error;
 
-int fail(int code, const std::string& msg) {
-  g_last_error = msg;
-  return code;
-}
+int fail(int code, const std::string& msg) { return cortex::record_error(code, msg.c_str()); }
 
 #define CUDA_TRY(expr)                                                                                         \
   do {                                                                                                         \
@@ -641,6 +638,17 @@ const char* cortex_strerror(int code) {
 }
 
 const char* cortex_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+namespace cortex {
+int record_error(int code, const char* msg) {
+  g_last_error = msg;
+  return code;
+}
+}  // namespace cortex
+
+extern "C" {
 
 void cortex_free(cortex_net* net) {
   if (!net) return;

@@ -252,6 +252,8 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // host launch wrappers (defined in build.cu and step.cu)
 namespace cortex {
+// sets the calling thread's cortex_last_error() text and returns code (api.cu)
+int record_error(int code, const char* msg);
 cudaError_t launch_props(NetDev* nets, int n_nets, cudaStream_t s);
 cudaError_t launch_build_count_net(const NetDev* nets_dev, int net_idx, int32_t n, int first_group, int n_groups,
                                    int32_t tb, uint32_t* cnt, cudaStream_t s);

@@ -153,19 +153,25 @@ using namespace cortex;
 
 extern "C" int cortex_subgraph_noalloc(const cortex_params* params, uint64_t seed, int32_t t_begin, int32_t t_end,
                                        void* stream, int32_t* row_ptr, int32_t* tgt, int32_t* delay, float* weight) {
-  if (!params || !row_ptr || t_begin < 0 || t_end < t_begin) return CORTEX_ERR_ARG;
+  if (!params || !row_ptr || t_begin < 0 || t_end < t_begin)
+    return record_error(CORTEX_ERR_ARG, "cortex_subgraph_noalloc: params / row_ptr NULL or bad target range");
   const cortex_params& c = *params;
   const int64_t n = (int64_t)c.n_exc + c.n_inh, k = (int64_t)c.k_exc + c.k_inh;
   if (c.n_exc < 0 || c.n_inh < 0 || n <= 0 || c.k_exc < 0 || c.k_inh < 0 || k > 65535 || t_end > n ||
       (c.k_exc > 0 && c.n_exc == 0) || (c.k_inh > 0 && c.n_inh == 0) || c.d_min < 1 || c.d_max < c.d_min ||
       (c.weight_dtype != CORTEX_F32 && c.weight_dtype != CORTEX_BF16))
-    return CORTEX_ERR_ARG;
+    return record_error(CORTEX_ERR_ARG, "cortex_subgraph_noalloc: invalid network parameters or t_end > n");
   const int64_t nnz = (t_end - t_begin) * k;
-  if (nnz > 0 && (!tgt || !delay || !weight)) return CORTEX_ERR_ARG;
-  if (t_end - t_begin > 65536) return CORTEX_ERR_UNSUPPORTED;           // local target in 16 bits
-  if ((size_t)(n + 1) + (size_t)nnz > kNoAllocWords) return CORTEX_ERR_UNSUPPORTED;  // scratch limit
+  if (nnz > 0 && (!tgt || !delay || !weight))
+    return record_error(CORTEX_ERR_ARG, "cortex_subgraph_noalloc: NULL output buffer");
+  if (t_end - t_begin > 65536)  // local target in 16 bits
+    return record_error(CORTEX_ERR_UNSUPPORTED, "cortex_subgraph_noalloc: more than 65536 targets in the range");
+  if ((size_t)(n + 1) + (size_t)nnz > kNoAllocWords)  // scratch limit
+    return record_error(CORTEX_ERR_UNSUPPORTED,
+                        "cortex_subgraph_noalloc: (n + 1) + targets * K above the 2^21 words of the static array");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return CORTEX_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
+    return record_error(CORTEX_ERR_CUDA, "cortex_subgraph_noalloc: no current CUDA device");
   void* base = nullptr;
   {
     // set-up, once per device (with that device current): the device address of the array
@@ -173,7 +179,7 @@ extern "C" int cortex_subgraph_noalloc(const cortex_params* params, uint64_t see
     if (!g_na_ptr[dev]) {
       if (cudaGetSymbolAddress(&g_na_ptr[dev], g_noalloc_scratch) != cudaSuccess) {
         g_na_ptr[dev] = nullptr;
-        return CORTEX_ERR_CUDA;
+        return record_error(CORTEX_ERR_CUDA, "cortex_subgraph_noalloc: cudaGetSymbolAddress of the static array failed");
       }
     }
     base = g_na_ptr[dev];
@@ -204,16 +210,19 @@ extern "C" int cortex_subgraph_noalloc(const cortex_params* params, uint64_t see
     k_na_fill<<<grid, 256, 0, s>>>(p, cnt, keys);
     const size_t smem = 8 * kNaSegCap * sizeof(uint32_t);
     if (cudaFuncSetAttribute(k_na_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return CORTEX_ERR_CUDA;
+      return record_error(CORTEX_ERR_CUDA, "cortex_subgraph_noalloc: kernel attribute");
     k_na_rows<<<grid, 256, smem, s>>>(p, row_ptr, keys, tgt, delay, weight, reinterpret_cast<int32_t*>(cnt + n));
   } else {
     k_na_scan<<<1, 1024, 0, s>>>(p, cnt, row_ptr);
   }
-  if (cudaGetLastError() != cudaSuccess) return CORTEX_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return record_error(CORTEX_ERR_CUDA, "cortex_subgraph_noalloc: kernel launch");
   uint32_t flags = 0;
-  if (cudaMemcpyAsync(&flags, cnt + n, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CORTEX_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return CORTEX_ERR_CUDA;
-  if (flags & 1u) return CORTEX_ERR_UNSUPPORTED;  // a source has more than 2048 synapses in the range
-  if (flags & 2u) return CORTEX_ERR_CUDA;
+  if (cudaMemcpyAsync(&flags, cnt + n, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return record_error(CORTEX_ERR_CUDA, "cortex_subgraph_noalloc: stream synchronisation");
+  if (flags & 1u)  // found on the device, after the outputs were partly written
+    return record_error(CORTEX_ERR_UNSUPPORTED,
+                        "cortex_subgraph_noalloc: a source has more than 2048 synapses in the range (outputs undefined)");
+  if (flags & 2u) return record_error(CORTEX_ERR_CUDA, "cortex_subgraph_noalloc: device consistency check failed");
   return CORTEX_OK;
 }

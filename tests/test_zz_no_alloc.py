@@ -53,3 +53,21 @@ def test_noalloc_rejects_sizes_beyond_its_array(cortex):
     with pytest.raises(cortex.CortexError) as e:
         cortex.subgraph_noalloc(spec, 1, 0, 1000, row, buf, buf, wt)
     assert e.value.code == cortex.ERR_UNSUPPORTED
+
+
+def test_noalloc_reports_a_source_over_its_per_source_cap(cortex):
+    """One inhibitory neuron drawn by every target of a 3,001-target range: that source has 3,001
+    synapses in the range, above the 2,048 a source may have.  The device finds it and the call
+    returns CORTEX_ERR_UNSUPPORTED with its own message (the outputs are then undefined)."""
+    import torch
+
+    spec = W.NetSpec(3000, 1, 1, 1)
+    n, nnz = spec.n, spec.n * spec.k
+    row = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    tg = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    dl = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    wt = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    with pytest.raises(cortex.CortexError) as e:
+        cortex.subgraph_noalloc(spec, 3, 0, n, row, tg, dl, wt)
+    assert e.value.code == cortex.ERR_UNSUPPORTED
+    assert "2048" in str(e.value)
