@@ -23,16 +23,40 @@ pytestmark = pytest.mark.gpu
 BENCH_OPTS = dict(steps_per_launch=1000)
 
 
-def _targets(spec, n_sample, seed):
+def _targets(spec, n_sample, seed, edges=()):
     rng = np.random.default_rng(seed)
     fixed = [0, spec.n_exc - 1, spec.n_exc, spec.n - 1]
-    return np.unique(np.concatenate([fixed, rng.integers(0, spec.n, n_sample)])).astype(np.int32)
+    return np.unique(np.concatenate([fixed, np.asarray(edges, np.int64),
+                                     rng.integers(0, spec.n, n_sample)])).astype(np.int32)
 
 
-def _replay_check(net, spec, seed, steps, net_idx=0, n_sample=40, sample_seed=0):
+def layout_edges(cortex, specs, opts):
+    """First and last target of every block and of every warp sub-range of each network, in the
+    plan the build makes (cortex_plan on this GPU): where the block and warp offsets, the 16-bit
+    piece offsets and the 12-bit warp ends of the layout change."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    smem = getattr(props, "shared_memory_per_block_optin", 232448)
+    tb, _ = cortex.plan(specs, opts, n_sm=props.multi_processor_count, smem_per_block=smem)
+    n_warps = min(opts.warps_per_block or 14, 16)
+    out = []
+    for spec, t in zip(specs, tb):
+        t = int(t)
+        tw = -(-t // n_warps)
+        e = []
+        for b0 in range(0, spec.n, t):
+            nt = min(t, spec.n - b0)
+            e += [b0, b0 + nt - 1]
+            for w0 in range(0, nt, tw):
+                e += [b0 + w0, b0 + min(w0 + tw, nt) - 1]
+        out.append(np.unique(np.asarray(e, np.int64)))
+    return out
+
+
+def _replay_check(net, spec, seed, steps, net_idx=0, n_sample=40, sample_seed=0, edges=()):
     gs, gi = net.spikes(net_idx)
     gv, gc, gr = net.state(net_idx)
-    tg = _targets(spec, n_sample, sample_seed)
+    tg = _targets(spec, n_sample, sample_seed, edges)
     ps, pi, (pv, pc, pr) = orc.replay(oracle_params(spec), seed, tg, steps, gs, gi)
     keep = np.isin(gi, tg)
     assert np.array_equal(ps, gs[keep]) and np.array_equal(pi, gi[keep]), "spikes of a sampled target differ"
@@ -42,29 +66,42 @@ def _replay_check(net, spec, seed, steps, net_idx=0, n_sample=40, sample_seed=0)
     return len(gs), int(keep.sum())
 
 
-@pytest.mark.parametrize("name,steps", [("c1", 1000), ("c2", 1000), ("c3", 500)])
-def test_full_size_sampled_targets_bit_exact(cortex, name, steps):
+@pytest.mark.parametrize("name,steps,delivery", [("c1", 1000, 0), ("c2", 1000, 0), ("c3", 500, 0),
+                                                 ("c2", 1000, 1), ("c3", 500, 1)])
+def test_full_size_sampled_targets_bit_exact(cortex, name, steps, delivery):
+    """Sampled targets, including the first and last of every block and warp sub-range (4,000+
+    targets at 152 blocks x 14 warps), replayed by the oracle from the GPU's raster."""
     cfg = W.CONFIGS[name]
     spec, seed = cfg["spec"], cfg["seed"]
-    with cortex.Network(spec, seed, cortex.make_options(**BENCH_OPTS)) as net:
+    opts = cortex.make_options(delivery=delivery, **BENCH_OPTS)
+    edges = layout_edges(cortex, [spec], opts)[0]
+    with cortex.Network(spec, seed, opts) as net:
         st = net.stats()
         assert st["n_synapses"] == spec.n * spec.k
         net.simulate(steps)
-        n_spikes, n_sampled = _replay_check(net, spec, seed, steps)
+        n_spikes, n_sampled = _replay_check(net, spec, seed, steps, edges=edges)
     assert n_spikes > steps, "the network should be active"
+    assert len(edges) > 2 * st["n_blocks"]
 
 
 @pytest.mark.slow
-def test_c1_raster_bit_exact_over_50ms(cortex):
-    """The whole raster of the 112,500-neuron network against the full FP32 oracle, 500 steps."""
-    cfg = W.CONFIGS["c1"]
-    spec, seed, steps = cfg["spec"], cfg["seed"], 500
-    with cortex.Network(spec, seed, cortex.make_options(**BENCH_OPTS)) as net:
+@pytest.mark.parametrize("name,steps,delivery", [("c1", 500, 0), ("c2", 300, 0), ("c2", 300, 1)])
+def test_whole_raster_bit_exact_against_the_full_oracle(cortex, name, steps, delivery):
+    """The whole raster, final state and event count of the 112,500-neuron network (500 steps) and of
+    the 500,000-neuron deep-delay network (2.5e9 synapses, 300 steps = five 6-step windows per 30
+    steps) against the full FP32 oracle, run target-partitioned on all host cores (bitwise equal to
+    the single-threaded oracle)."""
+    import os
+    cfg = W.CONFIGS[name]
+    spec, seed = cfg["spec"], cfg["seed"]
+    with cortex.Network(spec, seed, cortex.make_options(delivery=delivery, **BENCH_OPTS)) as net:
         net.simulate(steps)
         gs, gi = net.spikes()
         gv, gc, gr = net.state()
         st = net.stats()
-    ref, os_, oi, _ = oracle_run(spec, seed, steps)
+    ref = orc.Network(oracle_params(spec), seed, threads=max(1, os.cpu_count() or 1))
+    ref.simulate(steps)
+    os_, oi = ref.raster()
     assert len(os_) > 1000
     assert first_mismatch(gs, gi, os_, oi) == -1
     ov, oc, orr = ref.state()
@@ -75,15 +112,17 @@ def test_c1_raster_bit_exact_over_50ms(cortex):
 
 def test_batch_64_networks_sampled_targets_bit_exact(cortex):
     """The 64 uneven networks stepped together for 500 ms in the plan the autotuner picks (the one
-    the benchmark times); three targets of every instance."""
+    the benchmark times); the first and last target of every block and warp sub-range of every
+    instance, and random ones."""
     specs, seeds = W.batch_specs()
     steps = W.CONFIGS["c4"]["steps"]
     best, _, _ = cortex.autotune(specs, seeds, cortex.make_options(**BENCH_OPTS), trial_steps=500)
+    edges = layout_edges(cortex, specs, best)
     with cortex.Network(specs, seeds, best) as net:
         assert net.stats()["n_nets"] == 64
         net.simulate(steps)
         for b, (spec, seed) in enumerate(zip(specs, seeds)):
-            _replay_check(net, spec, seed, steps, net_idx=b, n_sample=2, sample_seed=b)
+            _replay_check(net, spec, seed, steps, net_idx=b, n_sample=2, sample_seed=b, edges=edges[b])
 
 
 def _rate_check(spec, s_a, i_a, s_b, i_b, t0, t1, block=250):

@@ -47,12 +47,14 @@ def test_noalloc_rejects_sizes_beyond_its_array(cortex):
     import torch
 
     spec = W.NetSpec(800000, 200000, 9000, 2250)
+    nnz = 1000 * spec.k  # buffers of the right size: the library's own limit refuses the request
     row = torch.empty(spec.n + 1, dtype=torch.int32, device="cuda")
-    buf = torch.empty(16, dtype=torch.int32, device="cuda")
-    wt = torch.empty(16, dtype=torch.float32, device="cuda")
+    buf = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    wt = torch.empty(nnz, dtype=torch.float32, device="cuda")
     with pytest.raises(cortex.CortexError) as e:
         cortex.subgraph_noalloc(spec, 1, 0, 1000, row, buf, buf, wt)
     assert e.value.code == cortex.ERR_UNSUPPORTED
+    assert "2^21" in str(e.value)
 
 
 def test_noalloc_reports_a_source_over_its_per_source_cap(cortex):
