@@ -145,6 +145,8 @@ typedef struct cortex_stats_t {
   int32_t exact_fold;                /* 1 if the delivery uses order-free adds (CORTEX_FOLD_EXACT) */
   int64_t l2_persist_bytes;          /* bytes of the ring in the persisting L2 window (0: none) */
   int32_t delivery;                  /* CORTEX_DELIVERY_* in use */
+  int64_t build_h2d_bytes;           /* host -> device bytes the build copied (its inputs: the
+                                        network parameters and the block plan) */
 } cortex_stats_t;
 
 typedef struct cortex_net cortex_net;

@@ -246,6 +246,7 @@ typedef struct oracle_net {
   /* target-partitioned form (oracle_build_par): part k owns targets [part_lo[k], part_lo[k+1])
    * and keeps its own CSR by source of their incoming synapses, sorted by (source, target, draw) */
   int32_t n_part;            /* 0: the single lists above */
+  int32_t sim_threads;       /* threads that step the parts (any number gives the same bits) */
   int64_t* part_lo;          /* [n_part + 1] */
   int64_t** prow;            /* [n_part][n + 1] */
   int32_t** ptgt;            /* [n_part][synapses of the part] */
@@ -558,6 +559,7 @@ int oracle_build_par(const oracle_params* p, uint64_t seed, int32_t n_part, orac
   net->pdly = (uint8_t**)xcalloc((size_t)n_part, sizeof(uint8_t*));
   if (!net->part_lo || !net->prow || !net->ptgt || !net->pdly) { oracle_free(net); return ORACLE_ERR_OOM; }
   net->n_part = n_part;
+  net->sim_threads = n_part;
   for (int32_t q = 0; q <= n_part; ++q) net->part_lo[q] = n * q / n_part;
   int failed = 0;
 #pragma omp parallel for num_threads(n_part) schedule(static, 1) reduction(| : failed)
@@ -591,6 +593,13 @@ int oracle_build_par(const oracle_params* p, uint64_t seed, int32_t n_part, orac
   return ORACLE_OK;
 }
 
+/* Threads that step the parts of a target-partitioned network (1 .. n_part). */
+int oracle_set_threads(oracle_net* net, int32_t threads) {
+  if (net->n_part < 1 || threads < 1) return ORACLE_ERR_ARG;
+  net->sim_threads = threads < net->n_part ? threads : net->n_part;
+  return ORACLE_OK;
+}
+
 /* Deliver the spike of source s emitted at step t onto the targets of part q (its own list). */
 static void deliver_part(oracle_net* net, int32_t q, int32_t s, int64_t t) {
   const int64_t* row = net->prow[q];
@@ -615,7 +624,7 @@ static int simulate_par(oracle_net* net, int64_t n_steps) {
   if (!emitted) return ORACLE_ERR_OOM;
   int rc = ORACLE_OK;
   const int32_t n_part = net->n_part;
-#pragma omp parallel num_threads(n_part)
+#pragma omp parallel num_threads(net->sim_threads)
   {
     for (int64_t step = 0; step < n_steps; ++step) {
       const int64_t t = net->step + step;

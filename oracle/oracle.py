@@ -94,6 +94,8 @@ def lib():
         L.oracle_build_edges.restype = ctypes.c_int
         L.oracle_build_par.argtypes = [P(_Params), ctypes.c_uint64, ctypes.c_int32, P(vp)]
         L.oracle_build_par.restype = ctypes.c_int
+        L.oracle_set_threads.argtypes = [vp, ctypes.c_int32]
+        L.oracle_set_threads.restype = ctypes.c_int
         L.oracle_free.argtypes = [vp]
         L.oracle_free.restype = None
         L.oracle_enable_accounting.argtypes = [vp]
@@ -344,6 +346,11 @@ class Network:
         if rc != 0:
             raise RuntimeError(f"oracle simulate failed: {rc}")
         return tr
+
+    def set_threads(self, threads: int):
+        """Threads that step a target-partitioned network (results do not depend on it)."""
+        if lib().oracle_set_threads(self._h, int(threads)) != 0:
+            raise ValueError("set_threads: only for a network built with threads > 1")
 
     def raster(self):
         n = int(lib().oracle_raster_size(self._h))

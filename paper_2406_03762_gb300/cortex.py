@@ -64,6 +64,7 @@ class Stats(ctypes.Structure):
         ("ring_in_smem", ctypes.c_int32), ("mode", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
         ("spikes_per_round", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
         ("exact_fold", ctypes.c_int32), ("l2_persist_bytes", ctypes.c_int64), ("delivery", ctypes.c_int32),
+        ("build_h2d_bytes", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -91,6 +91,7 @@ struct cortex_net {
   unsigned long long* bar_count = nullptr;
   int hist_max = 0;
   int64_t total_tbl = 0;
+  int64_t h2d_bytes = 0;  // host -> device bytes the build copied (network and block tables)
   bool l2_user = false;   // this handle raised the process's persisting-L2 limit
   int mode = CORTEX_MODE_PERSISTENT;
   int stage_bytes = 0, batch = 32;  // largest staging area, fewest spikes per round (stats)
@@ -616,6 +617,7 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
     h->batch = std::min(h->batch, bb);
   }
   CUDA_TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * nn, cudaMemcpyHostToDevice, h->stream));
+  h->h2d_bytes += (int64_t)(sizeof(NetDev) * nn);
   CUDA_TRY(step_kernel_attributes(h->smem));
   return CORTEX_OK;
 }
@@ -845,6 +847,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(cudaEventRecord(h->ev0, s), "event");
   TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * n_nets, cudaMemcpyHostToDevice, s), "upload nets");
   TRY(cudaMemcpyAsync(h->work_d, h->work_h.data(), sizeof(BlockWork) * h->n_blocks, cudaMemcpyHostToDevice, s), "upload work");
+  h->h2d_bytes += (int64_t)(sizeof(NetDev) * n_nets + sizeof(BlockWork) * h->n_blocks);
   TRY(cudaMemsetAsync(h->err, 0, 16, s), "memset");
   TRY(cudaMemsetAsync(h->max_seg, 0, 4 * (size_t)n_nets, s), "memset");
   TRY(cudaMemsetAsync(h->step_counter, 0, 16, s), "memset");
@@ -1138,6 +1141,7 @@ int cortex_stats(cortex_net* h, cortex_stats_t* st) {
   st->exact_fold = h->exact ? 1 : 0;
   st->l2_persist_bytes = (int64_t)h->apw.num_bytes;
   st->delivery = h->delivery;
+  st->build_h2d_bytes = h->h2d_bytes;
   if (h->delivery == CORTEX_DELIVERY_DELAY) {
     st->threads_per_block = h->d_threads;
     st->smem_bytes = (int32_t)h->d_smem;

@@ -78,11 +78,13 @@ CONFIGS = {
                name="batch64_brunel_n2k-50k"),
 }
 
-# Profiling cases: the c1 and c3 models at a quarter of the neurons and of the in-degree (same
+# Profiling cases: the c1, c2 and c3 models at a quarter of the neurons and of the in-degree (same
 # K/N, so the same per-block segment structure per source), small enough for ncu replay.
 PROFILE = {
     "c1q": dict(spec=NetSpec(22500, 5625, 2250, 562), steps=2000, seed=BASE_SEED + 11,
                 name="brunel_n28125_k2812_fp32"),
+    "c2q": dict(spec=NetSpec(100000, 25000, 1000, 250, d_min=5, d_max=40, nu_ext_hz=12000.0), steps=2000,
+                seed=BASE_SEED + 12, name="brunel_n125k_k1250_d5-40_fp32"),
     "c3q": dict(spec=NetSpec(200000, 50000, 2250, 562, weight_dtype=BF16), steps=2000, seed=BASE_SEED + 13,
                 name="brunel_n250k_k2812_bf16"),
 }
