@@ -87,6 +87,14 @@ PROFILE = {
                 seed=BASE_SEED + 12, name="brunel_n125k_k1250_d5-40_fp32"),
     "c3q": dict(spec=NetSpec(200000, 50000, 2250, 562, weight_dtype=BF16), steps=2000, seed=BASE_SEED + 13,
                 name="brunel_n250k_k2812_bf16"),
+    # DRAM-traffic cases: fewer neurons at the full in-degree, so a source's piece per block (K over
+    # the blocks) and the header share per synaptic event are those of the full configuration
+    "c1r": dict(spec=NetSpec(22500, 5625, 9000, 2250), steps=2000, seed=BASE_SEED + 21,
+                name="brunel_n28125_k11250_fp32"),
+    "c2r": dict(spec=NetSpec(100000, 25000, 4000, 1000, d_min=5, d_max=40, nu_ext_hz=12000.0), steps=2000,
+                seed=BASE_SEED + 22, name="brunel_n125k_k5000_d5-40_fp32"),
+    "c3r": dict(spec=NetSpec(40000, 10000, 9000, 2250, weight_dtype=BF16), steps=2000, seed=BASE_SEED + 23,
+                name="brunel_n50k_k11250_bf16"),
 }
 
 # Same statistics as c3 at 10,000 neurons (K = 11,250 > N, so sources repeat).
