@@ -40,6 +40,7 @@ extern "C" {
 #define CORTEX_ERR_TIMEOUT (-4)      /* a device-side wait gave up; the CUDA context stays usable */
 #define CORTEX_ERR_UNSUPPORTED (-5)  /* sizes outside the supported range, or no capable GPU */
 #define CORTEX_ERR_OVERFLOW (-6)     /* an output buffer was too small (needed size returned) */
+#define CORTEX_ERR_CHECK (-7)        /* ownership check: a ring cell was written by two warps */
 
 /* synaptic weight storage */
 #define CORTEX_F32 0                 /* float weights: 6 stored bytes per synapse (weight, u16 target/delay) */
@@ -121,6 +122,13 @@ typedef struct cortex_options {
                                         ring's size, at most the device maximum; the previous limit
                                         is restored when the last handle that raised it is freed */
   int32_t delivery;                  /* CORTEX_DELIVERY_* */
+  int32_t check_ownership;           /* debug mode, 0 = off.  1: the ownership check of Sec. IV-A
+                                        ("Verification": a synapse or post-synaptic neuron touched
+                                        by two threads is an error).  Every ring cell a delivery warp
+                                        writes is stamped with the warp's id; a cell written by a
+                                        second warp makes cortex_simulate return CORTEX_ERR_CHECK
+                                        (no trap).  Ring delivery only (CORTEX_ERR_UNSUPPORTED with
+                                        delay-ordered delivery); slower, and 4 more bytes per cell */
 } cortex_options;
 
 typedef struct cortex_stats_t {
@@ -198,6 +206,19 @@ int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t 
                     const cortex_options* base, int32_t trial_steps, void* stream,
                     cortex_options* best, double* best_ms_per_step, int32_t* n_tried,
                     float* net_work_out);
+
+/* cortex_autotune with a cache file (text, one line per tuned case, appended).  The key hashes
+ * (FNV-1a 64) the GPU's name, SM count and shared memory per block, every network's parameters and
+ * seed, the base options that shape a plan (ring, mode, targets_per_block, steps_per_launch,
+ * spikes_per_round, fold, delivery) and trial_steps.  On a hit the cached plan is returned without
+ * building anything (*hit = 1, *n_tried = 0, *best_ms_per_step the cached time); on a miss the
+ * candidates are tried as cortex_autotune does and the winner is appended (*hit = 0).  cache_path
+ * NULL: no cache.  hit may be NULL.  A line that does not parse is skipped; the last line with the
+ * key wins.  Same errors as cortex_autotune, plus CORTEX_ERR_ARG when the file cannot be written. */
+int cortex_autotune_cached(const cortex_params* params, const uint64_t* seeds, int32_t n_nets,
+                           const cortex_options* base, int32_t trial_steps, void* stream,
+                           const char* cache_path, cortex_options* best, double* best_ms_per_step,
+                           int32_t* n_tried, float* net_work_out, int32_t* hit);
 
 /* Advance every network by n_steps >= 0 steps from the current step (Sec. II-B loop: deliver,
  * update, compact spikes).  Continuing in pieces gives the same result as one call.
@@ -294,6 +315,24 @@ int cortex_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t*
  * or NULL outputs), CORTEX_ERR_UNSUPPORTED (size limits), CORTEX_ERR_CUDA. */
 int cortex_subgraph_noalloc(const cortex_params* params, uint64_t seed, int32_t t_begin, int32_t t_end,
                             void* stream, int32_t* row_ptr, int32_t* tgt, int32_t* delay, float* weight);
+
+/* Ownership stamps of network net_idx (built with check_ownership = 1): for every ring cell, the
+ * id of the warp that wrote it during the simulation, block * 16 + warp + 1 (block: the index in
+ * the handle's block list, the blocks of network b following those of networks 0..b-1), 0 if
+ * no delivery wrote it.  Host array of D * n words, slot-major like cortex_get_ring.  Errors:
+ * CORTEX_ERR_ARG (no stamps: check mode off), CORTEX_ERR_CUDA. */
+int cortex_get_stamps(cortex_net* net, int32_t net_idx, uint32_t* stamps);
+
+/* Host-only check of ownership stamps against the block plan (no device call): a network of n
+ * neurons cut into blocks of targets_per_block targets (the last may hold fewer), whose first block
+ * has index first_block, each block split into `warps` delivery sub-ranges of ceil(T_b / warps)
+ * targets.  The owner of target i is warp (i mod T_b) / ceil(T_b / warps) of block first_block +
+ * i / T_b; every nonzero stamp of a cell of target i (stamps: D * n words, slot-major) must name
+ * it.  *n_bad receives the number of cells stamped by another warp, *first_bad the index of the
+ * first of them (-1 if none).  Errors: CORTEX_ERR_ARG. */
+int cortex_check_stamps(int32_t n, int32_t depth, int32_t targets_per_block, int32_t warps,
+                        int32_t first_block, const uint32_t* stamps, int64_t* n_bad,
+                        int64_t* first_bad);
 
 /* Release everything the handle owns.  NULL is allowed. */
 void cortex_free(cortex_net* net);

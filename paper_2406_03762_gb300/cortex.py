@@ -13,7 +13,7 @@ import numpy as np
 from . import _build
 
 OK = 0
-ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OVERFLOW = -1, -2, -3, -4, -5, -6
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_OVERFLOW, ERR_CHECK = -1, -2, -3, -4, -5, -6, -7
 F32, BF16 = 0, 1
 RING_AUTO, RING_SMEM, RING_GLOBAL = 0, 1, 2
 MODE_PERSISTENT, MODE_SPLIT = 0, 1
@@ -47,6 +47,7 @@ class Options(ctypes.Structure):
         ("spikes_per_round", ctypes.c_int32), ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
         ("net_work", ctypes.POINTER(ctypes.c_float)),
         ("fold", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("delivery", ctypes.c_int32),
+        ("check_ownership", ctypes.c_int32),
     ]
 
     def work(self):
@@ -76,6 +77,7 @@ EXPORTED = [
     "cortex_stats", "cortex_export_synapses", "cortex_get_state", "cortex_constants", "cortex_deliver",
     "cortex_philox", "cortex_free", "cortex_strerror", "cortex_last_error", "cortex_subgraph_noalloc",
     "cortex_autotune", "cortex_get_ring", "cortex_set_state", "cortex_set_step", "cortex_plan",
+    "cortex_get_stamps", "cortex_check_stamps", "cortex_autotune_cached",
 ]
 
 _lib = None
@@ -118,6 +120,12 @@ def load(build_if_missing: bool = False):
     L.cortex_set_state.argtypes = [vp, ctypes.c_int32, P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_int32),
                                    P(ctypes.c_float)]
     L.cortex_set_step.argtypes = [vp, ctypes.c_int64]
+    L.cortex_autotune_cached.argtypes = [P(Params), P(ctypes.c_uint64), ctypes.c_int32, P(Options), ctypes.c_int32, vp,
+                                         ctypes.c_char_p, P(Options), P(ctypes.c_double), P(ctypes.c_int32),
+                                         P(ctypes.c_float), P(ctypes.c_int32)]
+    L.cortex_get_stamps.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint32)]
+    L.cortex_check_stamps.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      P(ctypes.c_uint32), P(ctypes.c_int64), P(ctypes.c_int64)]
     L.cortex_plan.argtypes = [P(Params), ctypes.c_int32, P(Options), ctypes.c_int32, ctypes.c_int64, P(ctypes.c_int32),
                               P(ctypes.c_int32)]
     L.cortex_autotune.argtypes = [P(Params), P(ctypes.c_uint64), ctypes.c_int32, P(Options), ctypes.c_int32, vp,
@@ -179,10 +187,12 @@ def _stream_handle(stream) -> int | None:
     return int(getattr(stream, "cuda_stream"))
 
 
-def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000, stream=None):
-    """cortex_autotune: the fastest plan (warps per block x block balance) for these networks.
-    Returns (Options, ms per simulation step, number of candidates built); a balance-2 plan keeps
-    its per-network costs alive with the returned Options."""
+def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000, stream=None, cache=None,
+             with_hit: bool = False):
+    """cortex_autotune (or cortex_autotune_cached with a cache file path): the fastest plan (warps
+    per block x block balance) for these networks.  Returns (Options, ms per simulation step,
+    number of candidates built) and, with with_hit, whether the cache answered; a balance-2 plan
+    keeps its per-network costs alive with the returned Options."""
     L = load()
     if not isinstance(specs, (list, tuple)):
         specs, seeds = [specs], [seeds]
@@ -191,14 +201,23 @@ def autotune(specs, seeds, base: Options | None = None, trial_steps: int = 1000,
     best = Options()
     ms = ctypes.c_double(0.0)
     n = ctypes.c_int32(0)
+    hit = ctypes.c_int32(0)
     work = (ctypes.c_float * len(specs))()
-    rc = L.cortex_autotune(arr, sd, len(specs), ctypes.byref(base) if base is not None else None, int(trial_steps),
-                           _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms), ctypes.byref(n), work)
+    if cache is None:
+        rc = L.cortex_autotune(arr, sd, len(specs), ctypes.byref(base) if base is not None else None,
+                               int(trial_steps), _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms),
+                               ctypes.byref(n), work)
+    else:
+        rc = L.cortex_autotune_cached(arr, sd, len(specs), ctypes.byref(base) if base is not None else None,
+                                      int(trial_steps), _stream_handle(stream), str(cache).encode(), ctypes.byref(best),
+                                      ctypes.byref(ms), ctypes.byref(n), work, ctypes.byref(hit))
     _check(rc, "cortex_autotune")
     if best.balance == 2:
         best._work = work  # best.net_work points into it
     else:
         best.net_work = None
+    if with_hit:
+        return best, float(ms.value), int(n.value), bool(hit.value)
     return best, float(ms.value), int(n.value)
 
 
@@ -311,6 +330,13 @@ class Network:
         _check(load().cortex_set_state(self._h, net_idx, _p(v, ctypes.c_float), _p(c, ctypes.c_float),
                                        _p(r, ctypes.c_int32), _p(g, ctypes.c_float)), "cortex_set_state")
 
+    def stamps(self, net_idx: int = 0) -> np.ndarray:
+        """cortex_get_stamps: [D, n] uint32, the warp that wrote each ring cell (check mode)."""
+        spec = self.specs[net_idx]
+        out = np.zeros((spec.d_max + 1, spec.n), np.uint32)
+        _check(load().cortex_get_stamps(self._h, net_idx, _p(out, ctypes.c_uint32)), "cortex_get_stamps")
+        return out
+
     def set_step(self, step: int):
         _check(load().cortex_set_step(self._h, int(step)), "cortex_set_step")
 
@@ -346,6 +372,19 @@ class Network:
         _check(load().cortex_deliver(self._h, net_idx, _p(a, ctypes.c_int32), len(a), int(t_emit), int(reps),
                                      ctypes.byref(ms), ctypes.byref(ev)), "cortex_deliver")
         return ms.value, ev.value
+
+
+def check_stamps(stamps: np.ndarray, targets_per_block: int, warps: int, first_block: int = 0):
+    """cortex_check_stamps (host only): (cells stamped by a warp that does not own them, index of
+    the first, -1 if none) for stamps [D, n] of one network."""
+    st = np.ascontiguousarray(stamps, np.uint32)
+    depth, n = st.shape
+    bad = ctypes.c_int64(0)
+    first = ctypes.c_int64(0)
+    _check(load().cortex_check_stamps(int(n), int(depth), int(targets_per_block), int(warps), int(first_block),
+                                      _p(st, ctypes.c_uint32), ctypes.byref(bad), ctypes.byref(first)),
+           "cortex_check_stamps")
+    return int(bad.value), int(first.value)
 
 
 def philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:

@@ -12,12 +12,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cortex.h"
 #include "cortex_internal.cuh"
 
 using namespace cortex;
 
 namespace {
+
+// NVTX range around a public call (visible in a profiler's timeline; free when no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 thread_local std::string g_last_error;
 
@@ -92,6 +100,8 @@ struct cortex_net {
   int hist_max = 0;
   int64_t total_tbl = 0;
   int64_t h2d_bytes = 0;  // host -> device bytes the build copied (network and block tables)
+  uint32_t* stamps = nullptr;            // ownership check: writer warp per ring cell
+  unsigned long long* viol = nullptr;    // ownership check: violations, first bad cell + 1
   bool l2_user = false;   // this handle raised the process's persisting-L2 limit
   int mode = CORTEX_MODE_PERSISTENT;
   int stage_bytes = 0, batch = 32;  // largest staging area, fewest spikes per round (stats)
@@ -382,6 +392,9 @@ int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_optio
   if (o.fold < CORTEX_FOLD_AUTO || o.fold > CORTEX_FOLD_EXACT) return fail(CORTEX_ERR_ARG, "fold must be 0..2");
   if (o.l2_persist < -1 || o.l2_persist > 1) return fail(CORTEX_ERR_ARG, "l2_persist must be -1, 0 or 1");
   if (o.delivery != CORTEX_DELIVERY_RING && o.delivery != CORTEX_DELIVERY_DELAY) return fail(CORTEX_ERR_ARG, "delivery");
+  if (o.check_ownership < 0 || o.check_ownership > 1) return fail(CORTEX_ERR_ARG, "check_ownership must be 0 or 1");
+  if (o.check_ownership && o.delivery == CORTEX_DELIVERY_DELAY)
+    return fail(CORTEX_ERR_UNSUPPORTED, "the ownership check stamps ring cells: ring delivery only");
   if (o.delivery == CORTEX_DELIVERY_DELAY) {
     if (o.mode == CORTEX_MODE_SPLIT) return fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery runs in persistent mode only");
     if (o.warps_per_block < 0 || o.warps_per_block > kDMaxWarps) return fail(CORTEX_ERR_ARG, "warps_per_block must be 1..32");
@@ -411,6 +424,15 @@ int check_err(cortex_net* h, const char* where) {
   if (e & kErrBuild) return fail(CORTEX_ERR_CUDA, std::string(where) + ": builder consistency check failed");
   if (e & kErrSegment) return fail(CORTEX_ERR_UNSUPPORTED, std::string(where) + ": a sub-graph segment exceeds the staging capacity");
   if (e & kErrRaster) return fail(CORTEX_ERR_OVERFLOW, std::string(where) + ": raster capacity exceeded");
+  if (h->viol) {
+    unsigned long long v[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(v, h->viol, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (v[0])
+      return fail(CORTEX_ERR_CHECK, std::string(where) + ": ownership check: " + std::to_string(v[0]) +
+                                        " ring cell writes by a second warp (first: global ring cell " +
+                                        std::to_string((long long)v[1] - 1) + ")");
+  }
   return CORTEX_OK;
 }
 
@@ -453,6 +475,8 @@ StepArgs make_args(cortex_net* h) {
   a.hist_cnt = h->hist_cnt;
   a.hist_max = h->hist_max;
   a.bar_count = h->bar_count;
+  a.stamps = h->stamps;
+  a.viol = h->viol;
   return a;
 }
 
@@ -635,6 +659,7 @@ const char* cortex_strerror(int code) {
     case CORTEX_ERR_TIMEOUT: return "device wait timed out";
     case CORTEX_ERR_UNSUPPORTED: return "unsupported size or configuration";
     case CORTEX_ERR_OVERFLOW: return "buffer too small";
+    case CORTEX_ERR_CHECK: return "ownership check failed";
     default: return "unknown status";
   }
 }
@@ -660,6 +685,7 @@ void cortex_free(cortex_net* net) {
 
 int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32_t n_nets, const cortex_options* opts,
                        void* stream, cortex_net** out) {
+  NvtxRange nvtx_range("cortex_build");
   if (!out) return fail(CORTEX_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!params || !seeds || n_nets <= 0) return fail(CORTEX_ERR_ARG, "params, seeds, n_nets");
@@ -835,6 +861,12 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   TRY(h->alloc(&h->err, 16), "alloc err");
   TRY(h->alloc(&h->step_counter, 16), "alloc step");
   TRY(h->alloc(&h->max_seg, 4 * (size_t)n_nets), "alloc max_seg");
+  if (o.check_ownership) {
+    TRY(h->alloc(&h->stamps, 4 * h->total_ring + 16), "alloc ownership stamps");
+    TRY(h->alloc(&h->viol, 16), "alloc ownership counters");
+    TRY(cudaMemsetAsync(h->stamps, 0, 4 * h->total_ring + 16, s), "memset stamps");
+    TRY(cudaMemsetAsync(h->viol, 0, 16, s), "memset ownership counters");
+  }
   if (h->delivery == CORTEX_DELIVERY_DELAY) {
     TRY(h->alloc(&h->dtgt, 2 * h->total_syn + 64), "alloc delay-ordered targets");
     TRY(h->alloc(&h->dw, wsz * h->total_syn + 64), "alloc delay-ordered weights");
@@ -961,6 +993,7 @@ int cortex_build(const cortex_params* params, uint64_t seed, const cortex_option
 int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t n_nets, const cortex_options* base,
                     int32_t trial_steps, void* stream, cortex_options* best, double* best_ms_per_step,
                     int32_t* n_tried, float* net_work_out) {
+  NvtxRange nvtx_range("cortex_autotune");
   if (!params || !seeds || n_nets <= 0 || trial_steps <= 0 || !best) return fail(CORTEX_ERR_ARG, "cortex_autotune: arguments");
   cortex_options b0;
   memset(&b0, 0, sizeof(b0));
@@ -1032,7 +1065,116 @@ int cortex_autotune(const cortex_params* params, const uint64_t* seeds, int32_t 
   return CORTEX_OK;
 }
 
+int cortex_autotune_cached(const cortex_params* params, const uint64_t* seeds, int32_t n_nets, const cortex_options* base,
+                           int32_t trial_steps, void* stream, const char* cache_path, cortex_options* best,
+                           double* best_ms_per_step, int32_t* n_tried, float* net_work_out, int32_t* hit) {
+  if (hit) *hit = 0;
+  if (!cache_path)
+    return cortex_autotune(params, seeds, n_nets, base, trial_steps, stream, best, best_ms_per_step, n_tried,
+                           net_work_out);
+  if (!params || !seeds || n_nets <= 0 || trial_steps <= 0 || !best)
+    return fail(CORTEX_ERR_ARG, "cortex_autotune_cached: arguments");
+  cortex_options b0;
+  memset(&b0, 0, sizeof(b0));
+  if (base) b0 = *base;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return fail(CORTEX_ERR_CUDA, "cortex_autotune_cached: device properties");
+  // FNV-1a 64 over the fields that decide the tuned plan
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) key = (key ^ c[i]) * 1099511628211ull;
+  };
+  mix(prop.name, strnlen(prop.name, sizeof(prop.name)));
+  mix(&prop.multiProcessorCount, sizeof(int));
+  mix(&prop.sharedMemPerBlockOptin, sizeof(size_t));
+  mix(&n_nets, sizeof(n_nets));
+  for (int b = 0; b < n_nets; ++b) {
+    mix(&params[b], sizeof(cortex_params));
+    mix(&seeds[b], sizeof(uint64_t));
+  }
+  const int32_t shape[7] = {b0.ring, b0.mode, b0.targets_per_block, b0.steps_per_launch, b0.spikes_per_round, b0.fold,
+                            b0.delivery};
+  mix(shape, sizeof(shape));
+  mix(&trial_steps, sizeof(trial_steps));
+  char khex[17];
+  snprintf(khex, sizeof(khex), "%016llx", (unsigned long long)key);
+  // lookup: "cortex-autotune-1 <key> <warps> <balance> <ms_per_step> <n_nets> <work_0> ... <work_{n-1}>"
+  if (FILE* f = fopen(cache_path, "r")) {
+    char line[65536];
+    bool found = false;
+    int w = 0, bal = 0, nn = 0;
+    double ms = 0;
+    std::vector<float> work;
+    while (fgets(line, sizeof(line), f)) {
+      char tag[32], k[32];
+      int used = 0;
+      int w2 = 0, b2 = 0, n2 = 0;
+      double ms2 = 0;
+      if (sscanf(line, "%31s %31s %d %d %lf %d%n", tag, k, &w2, &b2, &ms2, &n2, &used) != 6) continue;
+      if (strcmp(tag, "cortex-autotune-1") != 0 || strcmp(k, khex) != 0 || n2 != n_nets || b2 < 0 || b2 > 2 || w2 < 1 ||
+          w2 > kDMaxWarps)
+        continue;
+      std::vector<float> wk(n_nets, 0.0f);
+      const char* q = line + used;
+      bool ok = true;
+      for (int b = 0; b < n_nets && ok; ++b) {
+        int u = 0;
+        ok = sscanf(q, "%f%n", &wk[b], &u) == 1;
+        q += u;
+      }
+      if (!ok) continue;
+      found = true;
+      w = w2;
+      bal = b2;
+      ms = ms2;
+      nn = n2;
+      work.swap(wk);
+    }
+    fclose(f);
+    if (found && nn == n_nets && (bal != 2 || net_work_out)) {
+      *best = b0;
+      best->warps_per_block = w;
+      best->balance = bal;
+      best->net_work = nullptr;
+      if (bal == 2) {
+        std::copy(work.begin(), work.end(), net_work_out);
+        best->net_work = net_work_out;
+      }
+      if (best_ms_per_step) *best_ms_per_step = ms;
+      if (n_tried) *n_tried = 0;
+      if (hit) *hit = 1;
+      return CORTEX_OK;
+    }
+  }
+  double ms = 0;
+  int32_t tried = 0;
+  const int rc = cortex_autotune(params, seeds, n_nets, base, trial_steps, stream, best, &ms, &tried, net_work_out);
+  if (rc != CORTEX_OK) return rc;
+  if (best_ms_per_step) *best_ms_per_step = ms;
+  if (n_tried) *n_tried = tried;
+  FILE* f = fopen(cache_path, "a");
+  if (!f) return fail(CORTEX_ERR_ARG, std::string("cortex_autotune_cached: cannot append to ") + cache_path);
+  std::string line = std::string("cortex-autotune-1 ") + khex + " " + std::to_string(best->warps_per_block) + " " +
+                     std::to_string(best->balance) + " ";
+  char num[64];
+  snprintf(num, sizeof(num), "%.9g %d", ms, n_nets);
+  line += num;
+  for (int b = 0; b < n_nets; ++b) {
+    snprintf(num, sizeof(num), " %.9g", best->balance == 2 && best->net_work ? (double)best->net_work[b] : 0.0);
+    line += num;
+  }
+  line += "\n";
+  const bool wrote = fputs(line.c_str(), f) >= 0;
+  fclose(f);
+  if (!wrote) return fail(CORTEX_ERR_ARG, std::string("cortex_autotune_cached: cannot append to ") + cache_path);
+  return CORTEX_OK;
+}
+
 int cortex_simulate(cortex_net* h, int64_t n_steps) {
+  NvtxRange nvtx_range("cortex_simulate");
   if (!h || n_steps < 0) return fail(CORTEX_ERR_ARG, "cortex_simulate: handle / n_steps");
   if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_simulate: an earlier device wait timed out; free the handle");
   unsigned long long ev_before = 0;
@@ -1083,6 +1225,7 @@ int cortex_simulate(cortex_net* h, int64_t n_steps) {
 }
 
 int cortex_spikes(cortex_net* h, int32_t net_idx, int64_t* n_inout, int32_t* steps, int32_t* ids) {
+  NvtxRange nvtx_range("cortex_spikes");
   if (!h || !n_inout || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_spikes: arguments");
   unsigned long long c = 0;
   CUDA_TRY(cudaMemcpyAsync(&c, h->raster_count + net_idx, 8, cudaMemcpyDeviceToHost, h->stream));
@@ -1172,6 +1315,42 @@ int cortex_get_ring(cortex_net* h, int32_t net_idx, float* ring) {
                                4 * (size_t)w.nt, (size_t)d.depth, cudaMemcpyDeviceToHost, h->stream));
   }
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_get_stamps(cortex_net* h, int32_t net_idx, uint32_t* stamps) {
+  if (!h || !stamps || net_idx < 0 || net_idx >= h->n_nets) return fail(CORTEX_ERR_ARG, "cortex_get_stamps: arguments");
+  if (!h->stamps) return fail(CORTEX_ERR_ARG, "cortex_get_stamps: the handle was built without check_ownership");
+  const NetDev& d = h->nets_h[net_idx];
+  for (int g = 0; g < d.n_blocks; ++g) {
+    const BlockWork& w = h->work_h[d.first_block + g];
+    CUDA_TRY(cudaMemcpy2DAsync(stamps + w.t0, 4 * (size_t)d.n, h->stamps + w.ring_base, 4 * (size_t)w.nt,
+                               4 * (size_t)w.nt, (size_t)d.depth, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return CORTEX_OK;
+}
+
+int cortex_check_stamps(int32_t n, int32_t depth, int32_t targets_per_block, int32_t warps, int32_t first_block,
+                        const uint32_t* stamps, int64_t* n_bad, int64_t* first_bad) {
+  if (n <= 0 || depth <= 0 || targets_per_block <= 0 || warps <= 0 || warps > kMaxWarps || first_block < 0 ||
+      !stamps || !n_bad || !first_bad)
+    return fail(CORTEX_ERR_ARG, "cortex_check_stamps: arguments");
+  const int64_t tw = ceil_div(targets_per_block, warps);
+  int64_t bad = 0, first = -1;
+  for (int64_t s = 0; s < depth; ++s)
+    for (int64_t i = 0; i < n; ++i) {
+      const uint32_t st = stamps[s * n + i];
+      if (st == 0) continue;
+      const int64_t g = i / targets_per_block, local = i - g * targets_per_block;
+      const uint32_t owner = (uint32_t)((first_block + g) * kMaxWarps + local / tw) + 1u;
+      if (st != owner) {
+        if (first < 0) first = s * n + i;
+        ++bad;
+      }
+    }
+  *n_bad = bad;
+  *first_bad = first;
   return CORTEX_OK;
 }
 

@@ -149,6 +149,9 @@ struct StepArgs {
   uint32_t* hist_cnt;                 // [hist slot][n_blocks]: how many
   int32_t hist_max;                   // slots of the history arrays (largest hist_depth)
   unsigned long long* bar_count;      // per network: window arrivals of its blocks (monotonic)
+  // ownership check (debug): per ring cell the id of the warp that wrote it; violations
+  uint32_t* stamps;
+  unsigned long long* viol;           // [0] cells written by a second warp, [1] first such cell + 1
 };
 
 constexpr int kPhaseUpdate = 1;

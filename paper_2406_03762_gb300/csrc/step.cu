@@ -136,6 +136,21 @@ __device__ __forceinline__ void fold_four(float* ring, uint8_t* wtags, const uin
   }
 }
 
+// Ownership check (debug mode, Sec. IV-A "Verification": a synaptic interaction or post-synaptic
+// neuron touched by two threads is an error).  Every ring cell a delivery warp writes is stamped
+// with the warp's id (block * 16 + warp + 1) in a global array laid out like the global ring; a cell
+// found stamped by another warp is counted (viol[0]) and the first one recorded (viol[1] = cell + 1).
+// Nothing traps: the host reads the counters after the launch.
+__device__ __forceinline__ void stamp_cell(const StepArgs& a, int64_t ring_base, uint32_t key, uint32_t writer) {
+  if (key == 0xffffffffu) return;
+  const int64_t cell = ring_base + key;
+  const uint32_t old = atomicCAS(a.stamps + cell, 0u, writer);
+  if (old != 0u && old != writer) {
+    atomicAdd(a.viol, 1ull);
+    atomicCAS(a.viol + 1, 0ull, (unsigned long long)cell + 1ull);
+  }
+}
+
 // ---- the step kernel ---------------------------------------------------------------------------
 // phases: kPhaseUpdate, kPhaseDeliver, and kPhaseBarrier for the persistent form (both phases and
 // a barrier per window inside one cooperative launch of n_steps steps).  kRingSmem: the block's
@@ -707,6 +722,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         }
       }
       const uint32_t wbase_t = (uint32_t)(warp * tw);
+      const uint32_t writer = (uint32_t)(blk * kMaxWarps + warp) + 1u;  // ownership check: this warp's stamp
       uint8_t* wtags = kRingSmem ? tags : tags + (size_t)warp * kTagHash;
       const uint32_t lanes_lt = lanemask_lt();
       for (uint32_t r = 0; r < R; ++r) {
@@ -793,6 +809,9 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
             float wv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
+            if (a.stamps != nullptr)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) stamp_cell(a, wk.ring_base, key[u], writer);
             if constexpr (kExact) {
 #pragma unroll
               for (int u = 0; u < 4; ++u)
@@ -804,6 +823,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
           for (; e < total; e += 32) {
             float wv;
             const uint32_t key = chunk_key(e, wv);
+            if (a.stamps != nullptr) stamp_cell(a, wk.ring_base, key, writer);
             if constexpr (kExact) {
               if (key != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key, wv);
             } else {

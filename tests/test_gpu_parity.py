@@ -358,3 +358,20 @@ def test_host_plan_matches_the_build(cortex):
         _, nb = cortex.plan(specs, opts, n_sm=props.multi_processor_count, smem_per_block=smem)
         with cortex.Network(specs, seeds, opts) as net:
             assert net.stats()["n_blocks"] == nb, kw
+
+
+def test_autotune_cache_answers_the_second_call(cortex, tmp_path):
+    """cortex_autotune_cached: the first call tunes and appends the winner to the cache file, the
+    second returns the same plan without building anything; another network set misses."""
+    specs, seeds = W.small_batch_specs(n_nets=3)
+    path = tmp_path / "autotune.cache"
+    b1, ms1, n1, hit1 = cortex.autotune(specs, seeds, trial_steps=100, cache=path, with_hit=True)
+    assert not hit1 and n1 > 0 and path.exists()
+    b2, ms2, n2, hit2 = cortex.autotune(specs, seeds, trial_steps=100, cache=path, with_hit=True)
+    assert hit2 and n2 == 0 and abs(ms2 - ms1) <= 1e-6 * ms1
+    assert (b2.warps_per_block, b2.balance) == (b1.warps_per_block, b1.balance)
+    if b1.balance == 2:
+        assert np.allclose(b2.work(), b1.work())
+    _, _, _, hit3 = cortex.autotune(specs, [s + 1 for s in seeds], trial_steps=100, cache=path, with_hit=True)
+    assert not hit3
+    assert len(path.read_text().splitlines()) == 2
