@@ -64,7 +64,8 @@ extern "C" {
 #define CORTEX_DELIVERY_RING 0       /* a spike's synapses are read at emission and added into a ring
                                         of future input, D = d_max + 1 slots per neuron */
 #define CORTEX_DELIVERY_DELAY 1      /* delay-ordered (Sec. III-B "Varied Synaptic Delays", Sec. III-C
-                                        spike buffer): rows sorted by (delay, block, target); the
+                                        spike buffer): each block's piece of a row sorted by
+                                        (delay, target); the
                                         synapses of delay d of a spike at step e are read at step
                                         e + d into an accumulator of that step (d_min + 1 per neuron,
                                         in shared memory); the spikes of the last d_max steps are
@@ -72,8 +73,8 @@ extern "C" {
                                         Persistent mode only; no ring to export or restore
                                         (cortex_get_ring, cortex_set_state, cortex_set_step and
                                         cortex_deliver return CORTEX_ERR_UNSUPPORTED).  Needs
-                                        (d_max - d_min + 1) * blocks <= 8192 and (d_max + 1) *
-                                        (blocks + 2) <= 6400 for a network's blocks. */
+                                        (d_max + 1) * (blocks + 2) <= 6400 for a network's
+                                        blocks. */
 
 /* step-loop modes (cortex_options.mode) */
 #define CORTEX_MODE_PERSISTENT 0     /* one cooperative kernel per chunk, grid barrier inside */

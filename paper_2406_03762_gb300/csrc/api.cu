@@ -777,13 +777,10 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     d.raster_base = raster;
     d.raster_cap = rcap;
     raster += rcap;
-    d.tbl_stride = (p.d_max - p.d_min + 1) * nbk + 1;
+    d.tbl_stride = (p.d_max - p.d_min + 2) * nbk;  // per block: one offset per delay and the piece end
     d.tbl_base = h->total_tbl;
     d.hist_depth = p.d_max + d.window + 1;
     if (h->delivery == CORTEX_DELIVERY_DELAY) {
-      if ((p.d_max - p.d_min + 1) * nbk > kDLayCap)
-        return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: (d_max - d_min + 1) * blocks of a network above " +
-                                                     std::to_string(kDLayCap)));
       if ((p.d_max + 1) * (nbk + 2) > kDCntCap)
         return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: (d_max + 1) * (blocks + 2) of a network above " +
                                                      std::to_string(kDCntCap)));
@@ -868,8 +865,9 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     TRY(cudaMemsetAsync(h->viol, 0, 16, s), "memset ownership counters");
   }
   if (h->delivery == CORTEX_DELIVERY_DELAY) {
-    TRY(h->alloc(&h->dtgt, 2 * h->total_syn + 64), "alloc delay-ordered targets");
-    TRY(h->alloc(&h->dw, wsz * h->total_syn + 64), "alloc delay-ordered weights");
+    // BF16: one packed u32 per record (target, weight); FP32: u16 targets and float weights
+    TRY(h->alloc(&h->dtgt, h->wdtype == CORTEX_BF16 ? 64 : 2 * h->total_syn + 64), "alloc delay-ordered targets");
+    TRY(h->alloc(&h->dw, 4 * h->total_syn + 64), "alloc delay-ordered records");
     TRY(h->alloc(&h->dtbl, 2 * h->total_tbl + 64), "alloc delay tables");
     TRY(h->alloc(&h->hist_ids, 4 * (size_t)h->hist_max * h->n_total), "alloc spike buffer");
     TRY(h->alloc(&h->hist_cnt, 4 * (size_t)h->hist_max * h->n_blocks), "alloc spike buffer counts");

@@ -369,12 +369,16 @@ cudaError_t launch_build_finalize_net(const NetDev* nets_dev, const BlockWork* w
 
 // ---- delay-ordered layout (Sec. III-B "Varied Synaptic Delays": synapses reordered by delay) ---
 // From the CSR by source (row of source s grouped by block, by target inside a block), a second
-// copy of the records with each row sorted by (delay, block, target, draw), and per source a table
-// of u16 offsets in its row: tbl[(d - d_min) * nb + b] = first record of the (delay d, block b)
-// piece, tbl[n_delays * nb] = the row length.  A record keeps its block-local target (u16) and its
-// weight; the delay is the piece's.  Every (delay, block) piece is a stable subsequence of the
-// block's piece, so it stays in (target, draw) order.  One warp per source: count the pieces,
-// scan, scatter (ranks of equal delays inside a 32-entry chunk by __match_any_sync).
+// copy of the records in which every (source, block) piece is sorted by (delay, target, draw), and
+// per source a table of u16 offsets in its row: tbl[b * (n_delays + 1) + k] = first record of
+// block b's piece of delay d_min + k, tbl[b * (n_delays + 1) + n_delays] = the end of block b's
+// piece (for the last block: the row length).  A block's pieces of consecutive delays, and their
+// table entries, are adjacent, so the few pieces a spike contributes to one window share cache
+// lines.  A record keeps its block-local target and its weight (BF16: packed as one u32, target in
+// the low half; FP32: a u16 target array and a float weight array); the delay is the piece's.
+// Every delay piece is a stable subsequence of the block's piece, so it stays in (target, draw)
+// order.  One warp per source: per block, count the delays, scan, scatter (ranks of equal delays
+// inside a 32-entry chunk by __match_any_sync).
 __global__ void __launch_bounds__(128) k_delay_layout(const NetDev* __restrict__ nets,
                                                       const BlockWork* __restrict__ work, int net_idx, int n_dw,
                                                       const uint4* __restrict__ hdr,
@@ -383,56 +387,51 @@ __global__ void __launch_bounds__(128) k_delay_layout(const NetDev* __restrict__
                                                       const uint16_t* __restrict__ rec_meta,
                                                       uint16_t* __restrict__ dtbl, uint16_t* __restrict__ dtgt,
                                                       void* __restrict__ dw, int32_t* __restrict__ err) {
-  extern __shared__ uint32_t dl_cnt[];
+  __shared__ uint32_t dl_cnt[4][256 + 1];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t* c = dl_cnt + wib * kDLayCap;
+  uint32_t* c = dl_cnt[wib];
   const NetDev& d = nets[net_idx];
-  const int nb = d.n_blocks, n_del = d.d_max - d.d_min + 1, M = n_del * nb;
+  const int nb = d.n_blocks, n_del = d.d_max - d.d_min + 1;
   const uint32_t dmask = (1u << d.dbits) - 1u;
   const int64_t warp_global = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t warp_stride = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t s = warp_global; s < d.n; s += warp_stride) {
-    for (int q = lane; q < M; q += 32) c[q] = 0u;
-    __syncwarp();
     const int64_t r0 = d.rec_base + (int64_t)row_base[d.row_off + s];
-    // 1. entries per (delay, block) piece
-    for (int b = 0; b < nb; ++b) {
-      const int64_t hi = d.hdr_base + s * nb + b;
-      const uint4 h0 = hdr[2 * hi], h1 = hdr[2 * hi + 1];
-      const uint32_t words[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-      const uint32_t off = words[0] & 0xffffu, len = hdr_end(words, kMaxWarps - 1);
-      for (uint32_t q = lane; q < len; q += 32) atomicAdd(&c[(rec_meta[r0 + off + q] & dmask) * nb + b], 1u);
-    }
-    __syncwarp();
-    // 2. exclusive scan in (delay, block) order -> the table
-    uint32_t run = 0;
-    for (int q0 = 0; q0 < M; q0 += 32) {
-      const int q = q0 + lane;
-      const uint32_t v = q < M ? c[q] : 0u;
-      uint32_t x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (q < M) {
-        c[q] = run + x - v;
-        dtbl[d.tbl_base + s * d.tbl_stride + q] = (uint16_t)(run + x - v);
-      }
-      run += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) {
-      dtbl[d.tbl_base + s * d.tbl_stride + M] = (uint16_t)run;
-      if (run > 0xffffu) atomicOr(err, kErrSegment);
-    }
-    __syncwarp();
-    // 3. scatter, stable inside every (delay, block) piece
     for (int b = 0; b < nb; ++b) {
       const BlockWork wk = work[d.first_block + b];
       const int64_t hi = d.hdr_base + s * nb + b;
       const uint4 h0 = hdr[2 * hi], h1 = hdr[2 * hi + 1];
       const uint32_t words[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
       const uint32_t off = words[0] & 0xffffu, len = hdr_end(words, kMaxWarps - 1);
+      // 1. entries per delay of the piece
+      for (int q = lane; q <= n_del; q += 32) c[q] = 0u;
+      __syncwarp();
+      for (uint32_t q = lane; q < len; q += 32) atomicAdd(&c[rec_meta[r0 + off + q] & dmask], 1u);
+      __syncwarp();
+      // 2. exclusive scan over the delays -> the block's table row (offsets in the row)
+      uint32_t run = off;
+      uint16_t* trow = dtbl + d.tbl_base + s * d.tbl_stride + (int64_t)b * (n_del + 1);
+      for (int q0 = 0; q0 < n_del; q0 += 32) {
+        const int q = q0 + lane;
+        const uint32_t v = q < n_del ? c[q] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (q < n_del) {
+          c[q] = run + x - v;
+          trow[q] = (uint16_t)(run + x - v);
+        }
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
+      if (lane == 0) {
+        trow[n_del] = (uint16_t)run;
+        if (run > 0xffffu || run != off + len) atomicOr(err, kErrSegment);
+      }
+      __syncwarp();
+      // 3. scatter, stable inside every delay piece
       for (uint32_t q0 = 0; q0 < len; q0 += 32) {
         const uint32_t q = q0 + lane;
         const bool valid = q < len;
@@ -449,20 +448,22 @@ __global__ void __launch_bounds__(128) k_delay_layout(const NetDev* __restrict__
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, key);
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        const uint32_t cell = valid ? key * (uint32_t)nb + (uint32_t)b : 0u;
-        const uint32_t base = valid ? c[cell] : 0u;
+        const uint32_t base = valid ? c[key] : 0u;
         __syncwarp();
         if (valid) {
           const int64_t pos = r0 + base + rank;
-          dtgt[pos] = (uint16_t)local;
-          if (d.wdtype == 1) reinterpret_cast<__nv_bfloat16*>(dw)[pos] = __float2bfloat16_rn(w);
-          else reinterpret_cast<float*>(dw)[pos] = w;
-          if (rank == 0) c[cell] = base + (uint32_t)__popc(peers);
+          if (d.wdtype == 1) {
+            const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+            reinterpret_cast<uint32_t*>(dw)[pos] = local | ((uint32_t)__bfloat16_as_ushort(wb) << 16);
+          } else {
+            dtgt[pos] = (uint16_t)local;
+            reinterpret_cast<float*>(dw)[pos] = w;
+          }
+          if (rank == 0) c[key] = base + (uint32_t)__popc(peers);
         }
         __syncwarp();
       }
     }
-    __syncwarp();
   }
 }
 
@@ -470,12 +471,9 @@ cudaError_t launch_delay_layout(const NetDev* nets_dev, const NetDev* net_host, 
                                 int n_dw, const uint4* hdr, const unsigned long long* row_base, const void* rec_w,
                                 const uint16_t* rec_meta, uint16_t* dtbl, uint16_t* dtgt, void* dw, int32_t* err,
                                 cudaStream_t s) {
-  const size_t smem = 4 * kDLayCap * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(k_delay_layout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int blocks = (int)std::min<int64_t>(152 * 8, (net_host->n + 3) / 4);
-  k_delay_layout<<<std::max(blocks, 1), 128, smem, s>>>(nets_dev, work_dev, net_idx, n_dw, hdr, row_base, rec_w,
-                                                        rec_meta, dtbl, dtgt, dw, err);
+  k_delay_layout<<<std::max(blocks, 1), 128, 0, s>>>(nets_dev, work_dev, net_idx, n_dw, hdr, row_base, rec_w,
+                                                     rec_meta, dtbl, dtgt, dw, err);
   return cudaGetLastError();
 }
 

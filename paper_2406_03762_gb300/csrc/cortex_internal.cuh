@@ -55,7 +55,6 @@ constexpr int kInlMax = 3 * (kMboxWords - 1);  // spike ids a mailbox line carri
 constexpr int kDCntCap = 6400;
 constexpr int kDIdCap = 4096;
 constexpr int kDMaxWarps = 32;      // warps per block of the delay-ordered kernel
-constexpr int kDLayCap = 8192;      // (delay, block) pieces of one source the layout builder counts
 
 constexpr uint32_t kStreamConn = 1u;
 constexpr uint32_t kStreamV0 = 2u;
@@ -89,7 +88,7 @@ struct NetDev {
   int64_t raster_base, raster_cap;             // offset and capacity in the raster arrays
   // delay-ordered delivery (records sorted by source, delay, block, target, draw)
   int64_t tbl_base;                            // first table word of this network
-  int32_t tbl_stride;                          // table words per source: n_delays * n_blocks + 1
+  int32_t tbl_stride;                          // table words per source: (n_delays + 1) * n_blocks
   int32_t hist_depth;                          // steps of spike history kept: d_max + window + 1
   uint32_t thr[kPoissonCap];
 };
@@ -143,8 +142,8 @@ struct StepArgs {
   long long t_fixed;
   // delay-ordered delivery
   const uint16_t* dtgt;               // block-local target of every record (delay-ordered rows)
-  const void* dw;                     // weight of every record (f32 or bf16)
-  const uint16_t* dtbl;               // per source: offsets in its row of the (delay, block) pieces
+  const void* dw;                     // weight of every record (f32), or the packed record (bf16: target | w << 16)
+  const uint16_t* dtbl;               // per source and block: offsets in the row of the delay pieces
   uint32_t* hist_ids;                 // [hist slot][n_total]: ids a block emitted at a step
   uint32_t* hist_cnt;                 // [hist slot][n_blocks]: how many
   int32_t hist_max;                   // slots of the history arrays (largest hist_depth)

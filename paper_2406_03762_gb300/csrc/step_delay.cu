@@ -12,10 +12,11 @@
 // spikes of the last d_max steps: the spike buffer, kept in HBM (hist_ids / hist_cnt, d_max + W + 1
 // steps deep).
 //
-// Records (built once by k_delay_layout): each source's row sorted by (delay, block, target, draw),
-// with a table of u16 offsets of its (delay, block) pieces.  At arrival step T a block reads, for
-// every delay d and every source s that spiked at T - d, the piece (s, d, block).  All blocks read
-// their pieces of one (s, d) sub-row at the same step: the sub-row is contiguous in HBM.
+// Records (built once by k_delay_layout): each (source, block) piece of a row sorted by (delay,
+// target, draw), with a table of u16 offsets of its delay pieces.  At arrival step T a block reads,
+// for every delay d and every source s that spiked at T - d, the piece (s, block, d).  The pieces
+// of one spike for the W arrival steps of a window (consecutive delays) are adjacent, and so are
+// their table entries: the lanes that hold them share cache lines.
 //
 // Summation order of an accumulator cell (T, target): emission step ascending (= delay descending),
 // then source id ascending, then draw index -- the order of the oracle and of the ring kernel, so
@@ -96,7 +97,8 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
   const int d_min = ndg.d_min, d_max = ndg.d_max, H = ndg.hist_depth;
   const int64_t neuron_base = ndg.neuron_base, raster_base = ndg.raster_base, raster_cap = ndg.raster_cap;
   const int64_t rec_net = ndg.rec_base, row_off = ndg.row_off, tbl_net = ndg.tbl_base;
-  const int tbl_stride = ndg.tbl_stride, tbl_last = tbl_stride - 1;
+  const int tbl_stride = ndg.tbl_stride, tbl_last = tbl_stride - 1;  // last word: the row length
+  const int n_del1 = d_max - d_min + 2;  // table words per block: one per delay, and the piece end
   const int nt = wk.nt;
   const int tb_full = a.work[first_block].nt;
 
@@ -143,6 +145,21 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
         const int j = 4 * g + w - wk.t0;
         if (j >= 0 && j < nt) pk[sidx * nt + j] = (uint8_t)poisson_k(wd[w], nd, thr);
       }
+    }
+  };
+
+  // record r of the delay-ordered rows: block-local target and weight (BF16: one packed u32)
+  auto load_record = [&](unsigned long long r, bool ok, uint32_t& key, float& wv) {
+    key = 0xffffffffu;
+    wv = 0.0f;
+    if (!ok) return;
+    if constexpr (kBf16) {
+      const uint32_t x = reinterpret_cast<const uint32_t*>(a.dw)[r];
+      key = x & 0xffffu;
+      wv = __bfloat162float(__ushort_as_bfloat16((unsigned short)(x >> 16)));
+    } else {
+      key = a.dtgt[r];
+      wv = reinterpret_cast<const float*>(a.dw)[r];
     }
   };
 
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
           const long long e = e_lo + ide_s[gq];
           const int dly = (int)(Ta + ti - e);
           if (dly >= d_min && dly <= d_max) {
-            const int64_t tb = tbl_net + (int64_t)s * tbl_stride + (int64_t)(dly - d_min) * nb + wk.group;
+            const int64_t tb = tbl_net + (int64_t)s * tbl_stride + (int64_t)wk.group * n_del1 + (dly - d_min);
             const uint32_t lo = a.dtbl[tb], hi = a.dtbl[tb + 1];
             len = hi - lo;
             rec = (unsigned long long)rec_net + __ldg(a.row_base + row_off + s) + lo;
@@ -286,9 +303,7 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
             float wv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              key[u] = ok[u] ? (uint32_t)a.dtgt[r[u]] : 0xffffffffu;
-              if constexpr (kBf16) wv[u] = ok[u] ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.dw)[r[u]]) : 0.0f;
-              else wv[u] = ok[u] ? reinterpret_cast<const float*>(a.dw)[r[u]] : 0.0f;
+              load_record(r[u], ok[u], key[u], wv[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -311,13 +326,11 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
             float wv = 0.0f;
             if (q < total) {
               const unsigned long long r = rb + (q - st);
-              key = a.dtgt[r];
+              load_record(r, true, key, wv);
               if (key >= (uint32_t)nt) {  // not a target of this block: a layout error, recorded
                 atomicOr(a.err, kErrBuild);
                 key = 0xffffffffu;
               }
-              if constexpr (kBf16) wv = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.dw)[r]);
-              else wv = reinterpret_cast<const float*>(a.dw)[r];
             }
             fold_one<true>(acc_t_fixed, wtags, key, wv, lane, false);
           }
