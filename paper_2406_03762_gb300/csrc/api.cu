@@ -939,7 +939,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
       return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: the blocks cannot all be resident"));
     h->d_smem = 0;
     for (const NetDev& d : h->nets_h)
-      h->d_smem = std::max(h->d_smem, dstep_smem_bytes(h->work_h[d.first_block].nt, d.window, d.n_blocks,
+      h->d_smem = std::max(h->d_smem, dstep_smem_bytes(h->work_h[d.first_block].nt, d.window, d.n_blocks, d.d_max,
                                                        h->d_threads / 32, h->exact));
     if (h->d_smem > h->smem_cap)
       return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: the accumulators and state of a block need " +

@@ -278,7 +278,7 @@ cudaError_t launch_delay_layout(const NetDev* nets_dev, const NetDev* net_host, 
                                 const uint16_t* rec_meta, uint16_t* dtbl, uint16_t* dtgt, void* dw, int32_t* err,
                                 cudaStream_t s);
 cudaError_t launch_dstep(const StepArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
-size_t dstep_smem_bytes(int nt, int window, int nb, int n_warps, bool exact);
+size_t dstep_smem_bytes(int nt, int window, int nb, int d_max, int n_warps, bool exact);
 cudaError_t dstep_kernel_attributes(size_t smem);
 int dstep_occupancy(int threads, size_t smem);
 // apw: optional access-policy window of the launch (the ring kept resident in L2), NULL for none

@@ -43,9 +43,12 @@ struct DLayout {
   uint32_t acc, sv, si, sr, pk, thr, wcnt, wlist, ecnt, ids, ide, tags, total;
 };
 
+// (emission step, block) counts a delivery of a network needs, plus the raster's prefix pairs
+__host__ __device__ inline int dcount_words(int d_max, int nb) { return (d_max + 1) * (nb + 2); }
+
 __host__ __device__ inline uint32_t dalign(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline DLayout make_dlayout(int nt, int window, int n_warps, bool exact) {
+__host__ __device__ inline DLayout make_dlayout(int nt, int window, int n_warps, bool exact, int ncnt) {
   DLayout L;
   uint32_t o = 0;
   L.acc = o;  // window x nt accumulators: the input of the window's arrival steps
@@ -65,7 +68,7 @@ __host__ __device__ inline DLayout make_dlayout(int nt, int window, int n_warps,
   L.wlist = o;  // the step's spikes of each warp's sub-range (local ids, 16 bit)
   o = dalign(o + nt * 2, 16);
   L.ecnt = o;  // (emission step, block) spike counts of the window's delivery, then their prefixes
-  o += (kDCntCap + 1) * 4;
+  o = dalign(o + (uint32_t)(ncnt + 1) * 4, 16);
   L.ids = o;  // spike ids of the current chunk of emission steps
   o += kDIdCap * 4;
   L.ide = o;  // their emission step, relative to the first
@@ -102,7 +105,8 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
   const int nt = wk.nt;
   const int tb_full = a.work[first_block].nt;
 
-  const DLayout L = make_dlayout(tb_full, W, n_warps, kExact);
+  const int ncnt = dcount_words(d_max, nb);  // <= kDCntCap (checked by the build)
+  const DLayout L = make_dlayout(tb_full, W, n_warps, kExact, ncnt);
   float* acc = reinterpret_cast<float*>(smem + L.acc);
   float* sV = reinterpret_cast<float*>(smem + L.sv);
   float* sI = reinterpret_cast<float*>(smem + L.si);
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
     // emission steps whose spikes arrive in the window: e = T - d, d in [d_min, d_max]
     const long long e_lo = Ta - d_max, e_hi = Ta + Wd - 1 - d_min;
     const int n_e = (int)(e_hi - e_lo + 1);
-    const int E = n_e * nb;  // <= kDCntCap (checked by the build)
+    const int E = n_e * nb;  // < ncnt
     for (int q = tid; q < E; q += blockDim.x) {
       const long long e = e_lo + q / nb;
       ecnt[q] = e >= 0 ? __ldcg(a.hist_cnt + (int64_t)(e % H) * a.n_blocks + first_block + (q % nb)) : 0u;
@@ -223,32 +227,50 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
         const uint32_t* src = a.hist_ids + (int64_t)(e % H) * a.n_total + neuron_base + (int64_t)b * tb_full;
         const uint32_t k0 = o < g0 ? g0 - o : 0u, k1 = min(c, g1 - o);
         for (uint32_t k = k0; k < k1; ++k) {
-          ids_s[o + k - g0] = __ldcg(src + k);
+          const uint32_t id = __ldcg(src + k);
+          ids_s[o + k - g0] = id;
           ide_s[o + k - g0] = (uint16_t)ei;
         }
       }
       __syncthreads();
 
-      // One group of up to 32 pieces per warp pass: lane p holds piece p (spike index g, arrival
-      // step index ti), its first record and its length; the nonempty pieces are packed to the
-      // low lanes and their lengths scanned; then 32-entry chunks of the concatenated pieces, each
-      // lane finding its piece from the starts that fall inside the chunk.
-      auto fold_pieces = [&](uint32_t gq, int ti, bool valid, float* acc_t_fixed, uint8_t* wtags) {
-        // piece of spike gq (relative to g0) for arrival step Ta + ti
-        uint32_t len = 0;
-        unsigned long long rec = 0;
-        int tix = ti;
+      // Order-free fold: the loads of a piece (its table entries and row start).  Lanes hold the
+      // pieces of a spike for consecutive arrival steps, i.e. consecutive delays, whose
+      // table entries are adjacent: a piece's end is the next lane's start, unless the next lane is
+      // another spike, the next group, or past d_max (then the lane loads it too).
+      struct PieceLoad {
+        uint32_t lo, hi;
+        unsigned long long row;
+        bool in, own_end;
+        int ti;
+      };
+      auto piece_issue = [&](uint32_t gq, int ti, bool valid) {
+        PieceLoad pl;
+        pl.lo = pl.hi = 0;
+        pl.row = 0;
+        pl.in = pl.own_end = false;
+        pl.ti = ti;
         if (valid) {
           const uint32_t s = ids_s[gq];
           const long long e = e_lo + ide_s[gq];
           const int dly = (int)(Ta + ti - e);
           if (dly >= d_min && dly <= d_max) {
+            pl.in = true;
+            pl.own_end = ti == Wd - 1 || lane == 31 || dly == d_max;
             const int64_t tb = tbl_net + (int64_t)s * tbl_stride + (int64_t)wk.group * n_del1 + (dly - d_min);
-            const uint32_t lo = a.dtbl[tb], hi = a.dtbl[tb + 1];
-            len = hi - lo;
-            rec = (unsigned long long)rec_net + __ldg(a.row_base + row_off + s) + lo;
+            pl.lo = a.dtbl[tb];
+            if (pl.own_end) pl.hi = a.dtbl[tb + 1];
+            pl.row = __ldg(a.row_base + row_off + s);
           }
         }
+        return pl;
+      };
+
+      // One group of up to 32 pieces per warp pass: lane p holds piece p (its first record, length
+      // and arrival step index); the nonempty pieces are packed to the low lanes and their lengths
+      // scanned; then 32-entry chunks of the concatenated pieces, each lane finding its piece from
+      // the starts that fall inside the chunk.
+      auto fold_run = [&](uint32_t len, unsigned long long rec, int tix, float* acc_t_fixed, uint8_t* wtags) {
         const uint32_t ne = __ballot_sync(0xffffffffu, len > 0);
         const int n_ne = __popc(ne);
         if (n_ne == 0) return;
@@ -342,7 +364,11 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
         const uint32_t n_pc = n_ids * (uint32_t)Wd;
         for (uint32_t p0 = (uint32_t)warp * 32u; p0 < n_pc; p0 += (uint32_t)n_warps * 32u) {
           const uint32_t p = p0 + (uint32_t)lane;
-          fold_pieces(p / (uint32_t)Wd, (int)(p % (uint32_t)Wd), p < n_pc, nullptr, nullptr);
+          const PieceLoad pl = piece_issue(p / (uint32_t)Wd, (int)(p % (uint32_t)Wd), p < n_pc);
+          const uint32_t lo_next_lane = __shfl_down_sync(0xffffffffu, pl.lo, 1);
+          const uint32_t len = pl.in ? (pl.own_end ? pl.hi : lo_next_lane) - pl.lo : 0u;
+          const unsigned long long rec = pl.in ? (unsigned long long)rec_net + pl.row + pl.lo : 0ull;
+          fold_run(len, rec, pl.ti, nullptr, nullptr);
         }
       } else {
         // warp f folds arrival steps ti = f, f + n_fold, ...: its pieces in stream order
@@ -352,7 +378,20 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
             uint8_t* wtags = tags + (size_t)warp * tb_full;
             for (uint32_t p0 = 0; p0 < n_ids; p0 += 32u) {
               const uint32_t gq = p0 + (uint32_t)lane;
-              fold_pieces(gq, ti, gq < n_ids, acc_t, wtags);
+              uint32_t len = 0;
+              unsigned long long rec = 0;
+              if (gq < n_ids) {
+                const uint32_t s = ids_s[gq];
+                const long long e = e_lo + ide_s[gq];
+                const int dly = (int)(Ta + ti - e);
+                if (dly >= d_min && dly <= d_max) {
+                  const int64_t tb = tbl_net + (int64_t)s * tbl_stride + (int64_t)wk.group * n_del1 + (dly - d_min);
+                  const uint32_t lo = a.dtbl[tb], hi = a.dtbl[tb + 1];
+                  len = hi - lo;
+                  rec = (unsigned long long)rec_net + __ldg(a.row_base + row_off + s) + lo;
+                }
+              }
+              fold_run(len, rec, ti, acc_t, wtags);
             }
           }
         }
@@ -468,14 +507,14 @@ __global__ void __launch_bounds__(kWide ? kDMaxWarps * 32 : 16 * 32, 1) k_dstep(
         before = __reduce_add_sync(0xffffffffu, before);
         tot = __reduce_add_sync(0xffffffffu, tot);
         if (lane == 0) {
-          ecnt[kDCntCap - 2 * (ws + 1)] = before;  // past the counts (Wn * nb + 2 Wn <= kDCntCap)
-          ecnt[kDCntCap - 2 * (ws + 1) + 1] = tot;
+          ecnt[ncnt - 2 * (ws + 1)] = before;  // past the counts (Wn * nb + 2 Wn <= ncnt)
+          ecnt[ncnt - 2 * (ws + 1) + 1] = tot;
         }
       }
       __syncthreads();
       unsigned long long pos0 = raster_total;
       for (int ws = 0; ws < Wn; ++ws) {
-        const uint32_t before = ecnt[kDCntCap - 2 * (ws + 1)], tot = ecnt[kDCntCap - 2 * (ws + 1) + 1];
+        const uint32_t before = ecnt[ncnt - 2 * (ws + 1)], tot = ecnt[ncnt - 2 * (ws + 1) + 1];
         const uint32_t mine = ecnt[ws * nb + wk.group];
         const uint32_t* src = a.hist_ids + (int64_t)((t0 + ws) % H) * a.n_total + neuron_base + (int64_t)wk.group * tb_full;
         for (uint32_t q = tid; q < mine; q += blockDim.x) {
@@ -542,9 +581,8 @@ cudaError_t launch_dstep(const StepArgs& a, int grid, int threads, size_t smem, 
   return cudaLaunchKernelEx(&cfg, dstep_kernel(a.bf16 != 0, a.exact != 0, threads), a);
 }
 
-size_t dstep_smem_bytes(int nt, int window, int nb, int n_warps, bool exact) {
-  (void)nb;
-  return make_dlayout(nt, window, n_warps, exact).total;
+size_t dstep_smem_bytes(int nt, int window, int nb, int d_max, int n_warps, bool exact) {
+  return make_dlayout(nt, window, n_warps, exact, dcount_words(d_max, nb)).total;
 }
 
 cudaError_t dstep_kernel_attributes(size_t smem) {
