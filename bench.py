@@ -327,7 +327,7 @@ def our_arm(args):
         "plan": {"replicas": world, "blocks": st0["n_blocks"], "threads_per_block": st0["threads_per_block"],
                  "ring_in_smem": st0["ring_in_smem"], "spikes_per_round": st0["spikes_per_round"],
                  "smem_bytes": st0["smem_bytes"], "delivery": "delay" if args.delivery == 1 else "ring",
-                 "exact_fold": st0["exact_fold"]},
+                 "exact_fold": st0["exact_fold"], "helper_warp": st0["helper_warp"]},
         "rtf": rtf,
         "spikes": spikes, "events": events,
         "build_ms": st0["build_ms"],
@@ -427,7 +427,7 @@ def _form(cortex, W, name, kw, args, stream, peak, peak_kind, n_steps):
            "blocks": st0["n_blocks"], "threads_per_block": st0["threads_per_block"],
            "ring_in_smem": st0["ring_in_smem"], "spikes_per_round": st0["spikes_per_round"],
            "smem_bytes": st0["smem_bytes"], "delivery": "delay" if delivery == 1 else "ring",
-           "exact_fold": st0["exact_fold"], "dtype": "bf16" if bpe == 5 else "f32",
+           "exact_fold": st0["exact_fold"], "helper_warp": st0.get("helper_warp"), "dtype": "bf16" if bpe == 5 else "f32",
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "bytes_per_event": bpe,
                         "kernel": "k_dstep (persistent, delay-ordered)" if delivery == 1 else "k_step (persistent)",

@@ -130,6 +130,13 @@ typedef struct cortex_options {
                                         second warp makes cortex_simulate return CORTEX_ERR_CHECK
                                         (no trap).  Ring delivery only (CORTEX_ERR_UNSUPPORTED with
                                         delay-ordered delivery); slower, and 4 more bytes per cell */
+  int32_t helper_warp;               /* ring delivery: 1 = every block runs one more warp, which
+                                        fetches the piece headers and builds the copy and fold
+                                        descriptors of the coming rounds while the delivery warps
+                                        fold (warps_per_block stays the number of delivery warps, at
+                                        most 15); -1 = off; 0 = auto: on when the ring is in global
+                                        memory and the fold is ordered, in persistent mode.  Same
+                                        results. */
 } cortex_options;
 
 typedef struct cortex_stats_t {
@@ -156,6 +163,7 @@ typedef struct cortex_stats_t {
   int32_t delivery;                  /* CORTEX_DELIVERY_* in use */
   int64_t build_h2d_bytes;           /* host -> device bytes the build copied (its inputs: the
                                         network parameters and the block plan) */
+  int32_t helper_warp;               /* 1 if the ring kernel runs a helper warp per block */
 } cortex_stats_t;
 
 typedef struct cortex_net cortex_net;

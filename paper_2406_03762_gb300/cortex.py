@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
         ("spikes_per_round", ctypes.c_int32), ("balance", ctypes.c_int32), ("test_withhold_block", ctypes.c_int32),
         ("net_work", ctypes.POINTER(ctypes.c_float)),
         ("fold", ctypes.c_int32), ("l2_persist", ctypes.c_int32), ("delivery", ctypes.c_int32),
-        ("check_ownership", ctypes.c_int32),
+        ("check_ownership", ctypes.c_int32), ("helper_warp", ctypes.c_int32),
     ]
 
     def work(self):
@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
         ("ring_in_smem", ctypes.c_int32), ("mode", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
         ("spikes_per_round", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
         ("exact_fold", ctypes.c_int32), ("l2_persist_bytes", ctypes.c_int64), ("delivery", ctypes.c_int32),
-        ("build_h2d_bytes", ctypes.c_int64),
+        ("build_h2d_bytes", ctypes.c_int64), ("helper_warp", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -84,6 +84,7 @@ struct cortex_net {
   bool ring_smem = false;
   bool ring_red = false;  // global ring adds by the L2 reduction unit (exact for the weights)
   bool exact = false;     // every partial sum of a ring cell is exact: order-free adds
+  bool helper_warp = false;  // ring kernel: one more warp per block builds the piece descriptors
   int e_min = 0;          // exact: every weight is an integer multiple of 2^e_min
   double exact_bound = 0; // exact: largest |partial sum| of a cell, in units of 2^e_min
   cudaAccessPolicyWindow apw = {};  // the global ring, persisting in L2 (num_bytes 0: none)
@@ -393,6 +394,9 @@ int check_inputs(const cortex_params* params, int32_t n_nets, const cortex_optio
   if (o.l2_persist < -1 || o.l2_persist > 1) return fail(CORTEX_ERR_ARG, "l2_persist must be -1, 0 or 1");
   if (o.delivery != CORTEX_DELIVERY_RING && o.delivery != CORTEX_DELIVERY_DELAY) return fail(CORTEX_ERR_ARG, "delivery");
   if (o.check_ownership < 0 || o.check_ownership > 1) return fail(CORTEX_ERR_ARG, "check_ownership must be 0 or 1");
+  if (o.helper_warp < -1 || o.helper_warp > 1) return fail(CORTEX_ERR_ARG, "helper_warp must be -1, 0 or 1");
+  if (o.helper_warp > 0 && o.warps_per_block >= kMaxWarps)
+    return fail(CORTEX_ERR_ARG, "helper_warp needs warps_per_block <= 15 (the helper is one more warp)");
   if (o.check_ownership && o.delivery == CORTEX_DELIVERY_DELAY)
     return fail(CORTEX_ERR_UNSUPPORTED, "the ownership check stamps ring cells: ring delivery only");
   if (o.delivery == CORTEX_DELIVERY_DELAY) {
@@ -465,6 +469,7 @@ StepArgs make_args(cortex_net* h) {
   a.timeout_ns = h->timeout_ns;
   a.ring_red = h->ring_red ? 1 : 0;
   a.exact = h->exact ? 1 : 0;
+  a.helper_warp = h->helper_warp ? 1 : 0;
   a.bf16 = h->wdtype == CORTEX_BF16 ? 1 : 0;
   a.withhold_block = h->withhold_block;
   a.t_fixed = -1;
@@ -721,7 +726,8 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   } else {
     h->n_warps = o.warps_per_block ? o.warps_per_block : 14;
   }
-  h->threads = 32 * h->n_warps;
+  h->helper_warp = o.helper_warp > 0 && h->delivery == CORTEX_DELIVERY_RING;
+  h->threads = 32 * (h->n_warps + (h->helper_warp ? 1 : 0));
   h->mode = o.mode;
   h->steps_per_launch = o.steps_per_launch > 0 ? o.steps_per_launch : 1000;
   h->use_graph = o.use_graph >= 0;
@@ -933,6 +939,15 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     if (o.fold == CORTEX_FOLD_EXACT && !proven)
       return bail(fail(CORTEX_ERR_UNSUPPORTED, "fold EXACT: the weights do not make every partial sum of a ring cell exact"));
     h->exact = proven && o.fold != CORTEX_FOLD_ORDERED;
+  }
+  if (o.helper_warp == 0 && h->delivery == CORTEX_DELIVERY_RING && h->mode == CORTEX_MODE_PERSISTENT && !h->ring_smem &&
+      !h->exact && h->n_warps < kMaxWarps) {
+    // automatic helper warp: a global ring with the ordered fold (where it measured faster)
+    const int threads = 32 * (h->n_warps + 1);
+    if (step_occupancy(threads, h->smem, false) * h->n_sm >= h->n_blocks) {
+      h->helper_warp = true;
+      h->threads = threads;
+    }
   }
   if (h->delivery == CORTEX_DELIVERY_DELAY) {
     if (h->mode != CORTEX_MODE_PERSISTENT)
@@ -1274,6 +1289,7 @@ int cortex_stats(cortex_net* h, cortex_stats_t* st) {
   st->simulate_events = h->sim_events;
   st->n_blocks = h->n_blocks;
   st->threads_per_block = h->threads;
+  st->helper_warp = h->helper_warp ? 1 : 0;
   st->ring_in_smem = h->ring_smem ? 1 : 0;
   st->mode = h->mode;
   st->device_bytes = (int64_t)h->device_bytes;

@@ -136,6 +136,7 @@ struct StepArgs {
   int32_t bf16;                       // 1: weights stored as bf16 (all networks of a handle)
   int32_t ring_red;                   // 1: adds into a global ring use the L2 reduction unit
   int32_t exact;                      // 1: every partial sum of a ring cell is exact (order-free adds)
+  int32_t helper_warp;                // 1: the block's last warp builds descriptors, does not fold
   long long timeout_ns;
   int32_t withhold_block;             // test hook: this block never publishes (-1: none)
   // delivery-only launches (cortex_deliver): fixed emission step

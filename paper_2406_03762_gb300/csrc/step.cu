@@ -165,6 +165,10 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
   constexpr int kUpd = kRingSmem ? 1 : 4;
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
+  // delivery warps own the target sub-ranges of the layout; with a helper warp (the last one), that
+  // warp fetches the piece headers and builds the descriptors while the others fold
+  const int n_fold = n_warps - (a.helper_warp ? 1 : 0);
+  const int desc_tid = a.helper_warp ? tid - 32 * n_fold : tid;  // 0..31: the threads that do that work
   const int blk = blockIdx.x;
   const BlockWork wk = a.work[blk];
   const NetDev& ndg = a.nets[wk.net];
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
   const uint32_t B = (uint32_t)ndg.batch, cap_w = (uint32_t)ndg.cap_w, cap = (uint32_t)(ndg.cap_w + ndg.cap_m);
 
   // the network's own layout (its blocks' targets, depth, window and block count)
-  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes, n_warps);
+  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes, n_fold);
   float* ring_s = reinterpret_cast<float*>(smem + L.ring);
   float* sV = reinterpret_cast<float*>(smem + L.sv);
   float* sI = reinterpret_cast<float*>(smem + L.si);
@@ -676,7 +680,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         uint16_t* en = ends_slot(x) + k;
 #pragma unroll
         for (int q = 0; q < kMaxWarps; ++q)
-          if (q < n_warps) en[q * kSpikeBatch] = (uint16_t)hdr_end(hw, q);
+          if (q < n_fold) en[q * kSpikeBatch] = (uint16_t)hdr_end(hw, q);
       };
       // stage the records of round x: warp w copies spikes w, w + n_warps, ...; lane c copies the
       // 16-byte chunk c of the weight piece followed by the meta piece
@@ -685,7 +689,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         const uint4* ds = desc_slot(x);
         const uint32_t n = min(B, S_tot - x * B);
         unsigned char* sb = stage + (x % kStages) * (B * cap);
-        for (uint32_t k = warp; k < n; k += n_warps) {
+        for (uint32_t k = warp; k < n && warp < n_fold; k += n_fold) {
           const uint4 d0 = ds[2 * k];
           const uint32_t cnt = ds[2 * k + 1].x;
           const uint32_t nw = cnt & 0xffffu, nt2 = nw + (cnt >> 16);
@@ -729,18 +733,18 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         issue_round(r + kStages - 1);
         {
           const uint32_t xh = r + kHdrAhead;
-          if (tid < (int)B && xh < R && xh * B + tid < S_tot) fetch_hdr(xh, (uint32_t)tid);
+          if (desc_tid >= 0 && desc_tid < (int)B && xh < R && xh * B + desc_tid < S_tot) fetch_hdr(xh, (uint32_t)desc_tid);
         }
         cp_async_commit();
         cp_async_wait<kStages - 1>();
         __syncthreads();
         {
           const uint32_t xn = r + kStages;
-          if (tid < (int)B && xn < R && xn * B + tid < S_tot) store_desc(xn, (uint32_t)tid);
+          if (desc_tid >= 0 && desc_tid < (int)B && xn < R && xn * B + desc_tid < S_tot) store_desc(xn, (uint32_t)desc_tid);
         }
 
-        // ---- fold round r: each warp, its target sub-range of every staged piece, in spike order
-        {
+        // ---- fold round r: each delivery warp, its target sub-range of every staged piece, in spike order
+        if (warp < n_fold) {
           const uint32_t* aux_r = aux_slot(r);
           const uint16_t* ends_r = ends_slot(r);
           const uint32_t n = min(B, S_tot - r * B);

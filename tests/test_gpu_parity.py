@@ -101,6 +101,9 @@ MODES = [
     dict(warps_per_block=4, steps_per_launch=97),      # other warp split, odd launch chunks
     dict(warps_per_block=14, use_graph=-1),
     dict(warps_per_block=16, ring=2),                  # the widest block: 16 sub-range ends per header
+    dict(helper_warp=1),                               # one more warp builds the descriptors
+    dict(helper_warp=1, warps_per_block=13, ring=2),
+    dict(helper_warp=1, mode=1, warps_per_block=6),
 ]
 
 
