@@ -46,7 +46,7 @@ def test_traffic_is_reported_only_for_the_measured_kernel():
         found += 1
         with open(path) as f:
             rec = json.load(f)
-        assert 3.0 < rec["dram_bytes_per_event"] < 40.0
+        assert 3.0 < rec["dram_bytes_per_event"] < 60.0
         if rec["kernel_code_sha256"] == bench.kernel_digest(rec.get("kernel_name", "k_step")):
             assert bench._traffic(1e6, name) == rec["dram_bytes_per_event"] * 1e6
         else:
