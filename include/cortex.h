@@ -116,12 +116,14 @@ typedef struct cortex_options {
   const float* net_work;             /* balance 2: n_nets finite costs > 0 (any common unit), read
                                         by the build only; caller-owned; NULL otherwise */
   int32_t fold;                      /* CORTEX_FOLD_*: how delivery adds into a ring cell */
-  int32_t l2_persist;                /* ring in global memory: 0 = auto (on), 1 = on, -1 = off.
+  int32_t l2_persist;                /* ring in global memory: 0 = auto (off), 1 = on, -1 = off.
                                         On: the launches mark the ring as persisting in L2 (an
                                         access-policy window), and the build raises the process's
                                         persisting-L2 limit (cudaLimitPersistingL2CacheSize) to the
                                         ring's size, at most the device maximum; the previous limit
-                                        is restored when the last handle that raised it is freed */
+                                        is restored when the last handle that raised it is freed.
+                                        Off by default: the limit is process-wide state, and the
+                                        window changes the step time by about 1% */
   int32_t delivery;                  /* CORTEX_DELIVERY_* */
   int32_t check_ownership;           /* debug mode, 0 = off.  1: the ownership check of Sec. IV-A
                                         ("Verification": a synapse or post-synaptic neuron touched

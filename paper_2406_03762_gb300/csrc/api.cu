@@ -85,6 +85,7 @@ struct cortex_net {
   bool ring_red = false;  // global ring adds by the L2 reduction unit (exact for the weights)
   bool exact = false;     // every partial sum of a ring cell is exact: order-free adds
   bool helper_warp = false;  // ring kernel: one more warp per block builds the piece descriptors
+  bool no_auto_helper = false;  // the automatic helper warp was dropped (blocks not co-resident)
   int e_min = 0;          // exact: every weight is an integer multiple of 2^e_min
   double exact_bound = 0; // exact: largest |partial sum| of a cell, in units of 2^e_min
   cudaAccessPolicyWindow apw = {};  // the global ring, persisting in L2 (num_bytes 0: none)
@@ -599,6 +600,13 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   const int nn = h->n_nets;
   std::vector<int> cw(nn), cm(nn);
   std::vector<size_t> per(nn);  // staging bytes per spike of a round (kStages rounds in flight)
+  // the helper warp (it builds the descriptors and the delivery warps' segment tables): as asked,
+  // else automatic for the persistent kernel with the ring in global memory and the ordered fold
+  auto helper_for = [&](bool ring) {
+    if (h->delivery != CORTEX_DELIVERY_RING || h->n_warps >= kMaxWarps) return false;
+    if (o.helper_warp != 0) return o.helper_warp > 0;
+    return !h->no_auto_helper && h->mode == CORTEX_MODE_PERSISTENT && !ring && !h->exact;
+  };
   auto layout = [&](int b, bool ring, size_t stage) {
     const NetDev& d = h->nets_h[b];
     return step_smem_bytes(h->work_h[d.first_block].nt, d.depth, d.window, d.n_blocks, ring, (int)stage, h->n_warps);
@@ -622,6 +630,8 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
     return fail(CORTEX_ERR_UNSUPPORTED, std::string("shared memory too small for this plan (ring in ") +
                                             (smem_ring ? "shared" : "global") + " memory)");
   h->ring_smem = smem_ring;
+  h->helper_warp = helper_for(smem_ring);
+  h->threads = 32 * (h->n_warps + (h->helper_warp ? 1 : 0));
   {
     // reductions flush subnormals: allowed when every weight is 0 or >= 2^-102 in magnitude (with
     // margin for bf16 rounding), so that no partial sum of a cell can be subnormal
@@ -645,9 +655,13 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
     h->stage_bytes = std::max(h->stage_bytes, d.stage_bytes);
     h->batch = std::min(h->batch, bb);
   }
+  CUDA_TRY(step_kernel_attributes(h->smem));
+  if (h->helper_warp && o.helper_warp == 0 && step_occupancy(h->threads, h->smem, h->ring_smem) * h->n_sm < h->n_blocks) {
+    h->no_auto_helper = true;  // the automatic helper would keep the blocks from being co-resident
+    return choose_stage_and_ring(h, o);
+  }
   CUDA_TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * nn, cudaMemcpyHostToDevice, h->stream));
   h->h2d_bytes += (int64_t)(sizeof(NetDev) * nn);
-  CUDA_TRY(step_kernel_attributes(h->smem));
   return CORTEX_OK;
 }
 
@@ -921,6 +935,13 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->build_ms = ms;
 
+  {
+    // the fold: order-free adds when every partial sum of a cell is proven exact
+    const bool proven = prove_exact(h->nets_h, h->e_min, h->exact_bound);
+    if (o.fold == CORTEX_FOLD_EXACT && !proven)
+      return bail(fail(CORTEX_ERR_UNSUPPORTED, "fold EXACT: the weights do not make every partial sum of a ring cell exact"));
+    h->exact = proven && o.fold != CORTEX_FOLD_ORDERED;
+  }
   rc = choose_stage_and_ring(h, o);
   if (rc != CORTEX_OK) return bail(rc);
   if (h->mode == CORTEX_MODE_PERSISTENT && h->delivery == CORTEX_DELIVERY_RING) {
@@ -931,22 +952,6 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
       h->mode = CORTEX_MODE_SPLIT;  // not co-resident: fall back to split launches
       rc = choose_stage_and_ring(h, o);
       if (rc != CORTEX_OK) return bail(rc);
-    }
-  }
-  {
-    // the fold: order-free adds when every partial sum of a cell is proven exact
-    const bool proven = prove_exact(h->nets_h, h->e_min, h->exact_bound);
-    if (o.fold == CORTEX_FOLD_EXACT && !proven)
-      return bail(fail(CORTEX_ERR_UNSUPPORTED, "fold EXACT: the weights do not make every partial sum of a ring cell exact"));
-    h->exact = proven && o.fold != CORTEX_FOLD_ORDERED;
-  }
-  if (o.helper_warp == 0 && h->delivery == CORTEX_DELIVERY_RING && h->mode == CORTEX_MODE_PERSISTENT && !h->ring_smem &&
-      !h->exact && h->n_warps < kMaxWarps) {
-    // automatic helper warp: a global ring with the ordered fold (where it measured faster)
-    const int threads = 32 * (h->n_warps + 1);
-    if (step_occupancy(threads, h->smem, false) * h->n_sm >= h->n_blocks) {
-      h->helper_warp = true;
-      h->threads = threads;
     }
   }
   if (h->delivery == CORTEX_DELIVERY_DELAY) {
@@ -962,7 +967,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     TRY(dstep_kernel_attributes(h->d_smem), "delay kernel attributes");
     if (dstep_occupancy(h->d_threads, h->d_smem) * h->n_sm < h->n_blocks)
       return bail(fail(CORTEX_ERR_UNSUPPORTED, "delay-ordered delivery: the blocks cannot all be resident"));
-  } else if (!h->ring_smem && o.l2_persist >= 0) {
+  } else if (!h->ring_smem && o.l2_persist > 0) {
     l2_persist_acquire(h, 4 * h->total_ring);
   }
 #undef TRY

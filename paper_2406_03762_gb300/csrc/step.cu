@@ -106,32 +106,37 @@ __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window,
   return L;
 }
 
-// Fold four consecutive chunks with one tag array, software-pipelined: chunk u + 1 writes its
+// Fold N (1..4) consecutive chunks with one tag array, software-pipelined: chunk u + 1 writes its
 // tags as soon as chunk u's tags have been read (its ballot has consumed them), so that the tag
 // round trip of chunk u + 1 overlaps the ring updates of chunk u.  The __syncwarp that ends
-// chunk u's updates also orders chunk u + 1's tag writes before its tag reads.
-template <bool kRingSmem>
-__device__ __forceinline__ void fold_four(float* ring, uint8_t* wtags, const uint32_t* key, const float* w, int lane,
-                                          bool red) {
-  auto tag_of = [&](uint32_t k) -> uint8_t* {
-    return kRingSmem ? wtags + (k != 0xffffffffu ? k : 0u) : wtags + (k & (uint32_t)(kTagHash - 1));
-  };
-  uint8_t* tg = tag_of(key[0]);
-  if (key[0] != 0xffffffffu) *tg = (uint8_t)lane;
-  __syncwarp();
-  uint32_t t = key[0] != 0xffffffffu ? (uint32_t)*tg : (uint32_t)lane;
-  uint32_t losers = __ballot_sync(0xffffffffu, key[0] != 0xffffffffu && t != (uint32_t)lane);
+// chunk u's updates also orders chunk u + 1's tag writes before its tag reads, and chunk u's ring
+// updates before chunk u + 1's.
+template <bool kRingSmem, int N>
+__device__ __forceinline__ void fold_n(float* ring, uint8_t* wtags, const uint32_t* key, const float* w, int lane,
+                                       bool red) {
+  if constexpr (N == 1) {
+    fold_one<kRingSmem>(ring, wtags, key[0], w[0], lane, red);
+  } else {
+    auto tag_of = [&](uint32_t k) -> uint8_t* {
+      return kRingSmem ? wtags + (k != 0xffffffffu ? k : 0u) : wtags + (k & (uint32_t)(kTagHash - 1));
+    };
+    uint8_t* tg = tag_of(key[0]);
+    if (key[0] != 0xffffffffu) *tg = (uint8_t)lane;
+    __syncwarp();
+    uint32_t t = key[0] != 0xffffffffu ? (uint32_t)*tg : (uint32_t)lane;
+    uint32_t losers = __ballot_sync(0xffffffffu, key[0] != 0xffffffffu && t != (uint32_t)lane);
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    uint8_t* tgn = nullptr;
-    if (u < 3) {
-      tgn = tag_of(key[u + 1]);
-      if (key[u + 1] != 0xffffffffu) *tgn = (uint8_t)lane;
-    }
-    fold_apply<kRingSmem>(ring, key[u], w[u], t, losers, lane, red);  // ends with __syncwarp
-    if (u < 3) {
-      t = key[u + 1] != 0xffffffffu ? (uint32_t)*tgn : (uint32_t)lane;
-      losers = __ballot_sync(0xffffffffu, key[u + 1] != 0xffffffffu && t != (uint32_t)lane);
+    for (int u = 0; u < N; ++u) {
+      uint8_t* tgn = nullptr;
+      if (u + 1 < N) {
+        tgn = tag_of(key[u + 1]);
+        if (key[u + 1] != 0xffffffffu) *tgn = (uint8_t)lane;
+      }
+      fold_apply<kRingSmem>(ring, key[u], w[u], t, losers, lane, red);  // ends with __syncwarp
+      if (u + 1 < N) {
+        t = key[u + 1] != 0xffffffffu ? (uint32_t)*tgn : (uint32_t)lane;
+        losers = __ballot_sync(0xffffffffu, key[u + 1] != 0xffffffffu && t != (uint32_t)lane);
+      }
     }
   }
 }
@@ -647,49 +652,52 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         cp_async16(h + 16, hp + 1);
         cp_async8(h + 32, a.row_base + row_off + id);
       };
-      // piece descriptor of spike k of round x (one lane writes it).  For the copy (read by a whole
-      // warp, one spike at a time): [0] 16-byte-aligned global addresses of the weight and meta
-      // pieces, [1].x weight chunks | meta chunks << 16.  For the fold (read by lane k of every
-      // warp, so stored spike-minor to keep the lanes on distinct banks): aux[k] = weight offset |
-      // meta offset << 8 | emission slot << 16, and the header's end[w][k].
+      // Descriptors of round x, built by the 32 lanes of one warp (lane k: spike k of the round).
+      // For the copy: [0] 16-byte-aligned global addresses of the weight and meta pieces, [1].x
+      // weight chunks | meta chunks << 16.  For the fold (read by lane k of a warp, so stored spike-minor to keep
+      // the lanes on distinct banks): aux[k] = weight offset | meta offset << 8 | emission slot <<
+      // 16, and the header's end[w][k].
       auto desc_slot = [&](uint32_t x) { return desc_s + (x % (kStages + 1)) * (2 * kSpikeBatch); };
       auto aux_slot = [&](uint32_t x) {
         return reinterpret_cast<uint32_t*>(dsoa_s + (x % (kStages + 1)) * kSpikeBatch * (4 + 2 * kMaxWarps));
       };
       auto ends_slot = [&](uint32_t x) { return reinterpret_cast<uint16_t*>(aux_slot(x) + kSpikeBatch); };
-      auto store_desc = [&](uint32_t x, uint32_t k) {
-        const unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
-        const uint4 h0 = *reinterpret_cast<const uint4*>(h), h1 = *reinterpret_cast<const uint4*>(h + 16);
-        const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-        const unsigned long long row = *reinterpret_cast<const unsigned long long*>(h + 32);
-        const uint32_t g = x * B + k;
-        int ws = 0;
-        while (ws + 1 < Wn && woffs[ws + 1] <= g) ++ws;
-        const uint32_t len = hdr_end(hw, kMaxWarps - 1);
-        const unsigned long long r0 = (unsigned long long)rec_net + row + (h0.x & 0xffffu);
-        const unsigned long long wbyte = r0 * kWsz, mbyte = r0 * 2ull;
-        const uint32_t wal = (uint32_t)(wbyte & 15u), mal = (uint32_t)(mbyte & 15u);
-        const uint32_t nw = len ? (wal + len * kWsz + 15u) >> 4 : 0u;
-        const uint32_t nm = len ? (mal + len * 2u + 15u) >> 4 : 0u;
-        const unsigned long long gw = reinterpret_cast<unsigned long long>(a.rec_w) + (wbyte & ~15ull);
-        const unsigned long long gm = reinterpret_cast<unsigned long long>(a.rec_meta) + (mbyte & ~15ull);
-        uint4* d = desc_slot(x) + 2 * k;
-        d[0] = make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), (uint32_t)gm, (uint32_t)(gm >> 32));
-        d[1] = make_uint4(nw | (nm << 16), 0u, 0u, 0u);
-        aux_slot(x)[k] = wal | (mal << 8) | ((uint32_t)((tm0 + ws) % D) << 16);
-        uint16_t* en = ends_slot(x) + k;
+      auto store_desc = [&](uint32_t x) {
+        const uint32_t k = (uint32_t)lane, g = x * B + k;
+        const bool valid = k < B && g < S_tot;
+        uint32_t nw = 0, nm = 0;
+        if (valid) {
+          const unsigned char* h = hdr_s + ((x % kHdrSlots) * kSpikeBatch + k) * 48u;
+          const uint4 h0 = *reinterpret_cast<const uint4*>(h), h1 = *reinterpret_cast<const uint4*>(h + 16);
+          const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+          const unsigned long long row = *reinterpret_cast<const unsigned long long*>(h + 32);
+          int ws = 0;
+          while (ws + 1 < Wn && woffs[ws + 1] <= g) ++ws;
+          const uint32_t len = hdr_end(hw, kMaxWarps - 1);
+          const unsigned long long r0 = (unsigned long long)rec_net + row + (h0.x & 0xffffu);
+          const unsigned long long wbyte = r0 * kWsz, mbyte = r0 * 2ull;
+          const uint32_t wal = (uint32_t)(wbyte & 15u), mal = (uint32_t)(mbyte & 15u);
+          nw = len ? (wal + len * kWsz + 15u) >> 4 : 0u;
+          nm = len ? (mal + len * 2u + 15u) >> 4 : 0u;
+          const unsigned long long gw = reinterpret_cast<unsigned long long>(a.rec_w) + (wbyte & ~15ull);
+          const unsigned long long gm = reinterpret_cast<unsigned long long>(a.rec_meta) + (mbyte & ~15ull);
+          desc_slot(x)[2 * k] = make_uint4((uint32_t)gw, (uint32_t)(gw >> 32), (uint32_t)gm, (uint32_t)(gm >> 32));
+          aux_slot(x)[k] = wal | (mal << 8) | ((uint32_t)((tm0 + ws) % D) << 16);
+          uint16_t* en = ends_slot(x) + k;
 #pragma unroll
-        for (int q = 0; q < kMaxWarps; ++q)
-          if (q < n_fold) en[q * kSpikeBatch] = (uint16_t)hdr_end(hw, q);
+          for (int q = 0; q < kMaxWarps; ++q)
+            if (q < n_fold) en[q * kSpikeBatch] = (uint16_t)hdr_end(hw, q);
+        }
+        if (valid) desc_slot(x)[2 * k + 1] = make_uint4(nw | (nm << 16), 0u, 0u, 0u);
       };
-      // stage the records of round x: warp w copies spikes w, w + n_warps, ...; lane c copies the
-      // 16-byte chunk c of the weight piece followed by the meta piece
+      // stage the records of round x: delivery warp w copies spikes w, w + n_fold, ...; lane c
+      // copies the 16-byte chunk c of the weight piece followed by the meta piece
       auto issue_round = [&](uint32_t x) {
-        if (x >= R) return;
+        if (x >= R || warp >= n_fold) return;
         const uint4* ds = desc_slot(x);
         const uint32_t n = min(B, S_tot - x * B);
         unsigned char* sb = stage + (x % kStages) * (B * cap);
-        for (uint32_t k = warp; k < n && warp < n_fold; k += n_fold) {
+        for (uint32_t k = warp; k < n; k += n_fold) {
           const uint4 d0 = ds[2 * k];
           const uint32_t cnt = ds[2 * k + 1].x;
           const uint32_t nw = cnt & 0xffffu, nt2 = nw + (cnt >> 16);
@@ -703,18 +711,19 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
           }
         }
       };
-
-      // Pipeline (iteration r): issue the records of round r + kStages - 1 and the headers of round
-      // r + kHdrAhead; wait until round r's copy group is complete; build the descriptors of round
+      const uint32_t lanes_lt = lanemask_lt();
+      // Pipeline (iteration r): wait until round r's copy group is complete (committed kStages - 1
+      // iterations earlier) and meet at the round's barrier; build the descriptors of round
       // r + kStages from headers fetched kHdrAhead - kStages iterations earlier (whose groups are
-      // complete by then since kHdrAhead >= 2 kStages - 1); fold round r.
+      // complete by then since kHdrAhead >= 2 kStages - 1); fold round r; then, without another
+      // barrier, issue the records of round r + kStages - 1 into the slot of round r - 1 (every
+      // warp finished folding round r - 1 before this round's barrier) and the headers of round
+      // r + kHdrAhead.  One barrier per round; the window's last folds meet the update at the
+      // barrier after the loop.
       if (R > 0) {
         // descriptors of the first kStages rounds (their headers were copied with the ids), then the
         // headers of rounds kStages .. kHdrAhead - 1 and the records of the first kStages - 1 rounds
-        for (uint32_t i = tid; i < min(R, (uint32_t)kStages) * B; i += blockDim.x) {
-          const uint32_t x = i / B, k = i % B;
-          if (x * B + k < S_tot) store_desc(x, k);
-        }
+        for (uint32_t x = (uint32_t)warp; x < min(R, (uint32_t)kStages); x += (uint32_t)n_warps) store_desc(x);
         __syncthreads();
         for (uint32_t i = tid; i < (uint32_t)(kHdrAhead - kStages) * B; i += blockDim.x) {
           const uint32_t x = kStages + i / B, k = i % B;
@@ -728,23 +737,16 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
       const uint32_t wbase_t = (uint32_t)(warp * tw);
       const uint32_t writer = (uint32_t)(blk * kMaxWarps + warp) + 1u;  // ownership check: this warp's stamp
       uint8_t* wtags = kRingSmem ? tags : tags + (size_t)warp * kTagHash;
-      const uint32_t lanes_lt = lanemask_lt();
       for (uint32_t r = 0; r < R; ++r) {
-        issue_round(r + kStages - 1);
-        {
-          const uint32_t xh = r + kHdrAhead;
-          if (desc_tid >= 0 && desc_tid < (int)B && xh < R && xh * B + desc_tid < S_tot) fetch_hdr(xh, (uint32_t)desc_tid);
-        }
-        cp_async_commit();
-        cp_async_wait<kStages - 1>();
+        cp_async_wait<kStages - 2>();
         __syncthreads();
-        {
-          const uint32_t xn = r + kStages;
-          if (desc_tid >= 0 && desc_tid < (int)B && xn < R && xn * B + desc_tid < S_tot) store_desc(xn, (uint32_t)desc_tid);
-        }
+        if (desc_tid >= 0 && desc_tid < 32 && r + kStages < R) store_desc(r + kStages);  // the helper, else warp 0
 
         // ---- fold round r: each delivery warp, its target sub-range of every staged piece, in spike order
         if (warp < n_fold) {
+          // the warp's segments (spikes with entries in its sub-range), in spike order: per lane,
+          // the first entry of segment `lane` in the warp's stream of the round, the staging
+          // addresses of entry 0 as if the segment started there, the emission slot + d_min
           const uint32_t* aux_r = aux_slot(r);
           const uint16_t* ends_r = ends_slot(r);
           const uint32_t n = min(B, S_tot - r * B);
@@ -783,61 +785,80 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
           }
           const uint32_t c_start = c_end - c_len;
           const uint32_t total = __shfl_sync(0xffffffffu, c_end, 31);
-          if (lane == 0) my_events += total;
-          // per segment: staging addresses of entry q are base + q * size (q counts over the round)
+          // staging addresses of entry q of a segment: base + q * size (q counts over the round)
           const uint32_t c_wadj = c_wb - c_start * kWsz, c_madj = c_mb - c_start * 2u;
-          int cur = -1;
-          // key and weight of the lane's entry in the chunk starting at cb (0xffffffff: none)
-          auto chunk_key = [&](uint32_t cb, float& wv) -> uint32_t {
-            const uint32_t bits = (lane < n_ne && c_start - cb < 32u) ? (1u << (c_start - cb)) : 0u;
-            const uint32_t sm = __reduce_or_sync(0xffffffffu, bits);
-            const int seg = cur + __popc(sm & (lanes_lt | (1u << lane)));
-            cur += __popc(sm);
-            const int sl = seg & 31;
-            const uint32_t wa = __shfl_sync(0xffffffffu, c_wadj, sl);
-            const uint32_t ma = __shfl_sync(0xffffffffu, c_madj, sl);
-            const uint32_t sbv = __shfl_sync(0xffffffffu, c_sb, sl);
-            const uint32_t q = cb + lane;
-            wv = 0.0f;
-            if (q >= total) return 0xffffffffu;
-            const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + ma + 2u * q);
-            if constexpr (kBf16) wv = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + wa + 2u * q));
-            else wv = *reinterpret_cast<const float*>(stage + wa + 4u * q);
-            uint32_t slot = sbv + (meta & dmask);
-            if (slot >= (uint32_t)D) slot -= (uint32_t)D;
-            return slot * (uint32_t)nt + wbase_t + (meta >> dbits);
-          };
+          if (lane == 0) my_events += total;
+          int cur = -1;  // segment of the entry before the next chunk
+          // the warp's chunks of 32 entries, up to four at a time.  Keys (ring cells, 0xffffffff:
+          // no entry) and weights of all of a group's chunks are found step by step across the
+          // chunks (segment starts, segment of each lane's entry, its staging addresses, its
+          // record), so that the chunks' dependency chains overlap; then their ring updates run
+          // in chunk order.
           uint32_t e = 0;
-          for (; e + 3 * 32 < total; e += 4 * 32) {  // four chunks at a time while they are all used
-            uint32_t key[4];
-            float wv[4];
+          auto fold_group = [&](auto nc) {
+            constexpr int N = decltype(nc)::value;
+            uint32_t key[N], sm[N], wa[N], ma[N], sbv[N];
+            int sl[N];
+            float wv[N];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) key[u] = chunk_key(e + 32u * u, wv[u]);
+            for (int u = 0; u < N; ++u) {
+              const uint32_t cb = e + 32u * u;
+              sm[u] = __reduce_or_sync(0xffffffffu, (lane < n_ne && c_start - cb < 32u) ? (1u << (c_start - cb)) : 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+              sl[u] = (cur + __popc(sm[u] & (lanes_lt | (1u << lane)))) & 31;
+              cur += __popc(sm[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < N; ++u) wa[u] = __shfl_sync(0xffffffffu, c_wadj, sl[u]);
+#pragma unroll
+            for (int u = 0; u < N; ++u) ma[u] = __shfl_sync(0xffffffffu, c_madj, sl[u]);
+#pragma unroll
+            for (int u = 0; u < N; ++u) sbv[u] = __shfl_sync(0xffffffffu, c_sb, sl[u]);
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+              const uint32_t q = e + 32u * u + lane;
+              key[u] = 0xffffffffu;
+              wv[u] = 0.0f;
+              if (q < total) {
+                const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + ma[u] + 2u * q);
+                if constexpr (kBf16) wv[u] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + wa[u] + 2u * q));
+                else wv[u] = *reinterpret_cast<const float*>(stage + wa[u] + 4u * q);
+                uint32_t slot = sbv[u] + (meta & dmask);
+                if (slot >= (uint32_t)D) slot -= (uint32_t)D;
+                key[u] = slot * (uint32_t)nt + wbase_t + (meta >> dbits);
+              }
+            }
             if (a.stamps != nullptr)
 #pragma unroll
-              for (int u = 0; u < 4; ++u) stamp_cell(a, wk.ring_base, key[u], writer);
+              for (int u = 0; u < N; ++u) stamp_cell(a, wk.ring_base, key[u], writer);
             if constexpr (kExact) {
 #pragma unroll
-              for (int u = 0; u < 4; ++u)
+              for (int u = 0; u < N; ++u)
                 if (key[u] != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key[u], wv[u]);
             } else {
-              fold_four<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
+              fold_n<kRingSmem, N>(ring, wtags, key, wv, lane, ring_red);
             }
-          }
-          for (; e < total; e += 32) {
-            float wv;
-            const uint32_t key = chunk_key(e, wv);
-            if (a.stamps != nullptr) stamp_cell(a, wk.ring_base, key, writer);
-            if constexpr (kExact) {
-              if (key != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key, wv);
-            } else {
-              fold_one<kRingSmem>(ring, wtags, key, wv, lane, ring_red);
-            }
+            e += 32u * N;
+          };
+          while (e < total) {
+            const uint32_t left = (total - e + 31u) >> 5;
+            if (left >= 4u) fold_group(std::integral_constant<int, 4>());
+            else if (left == 3u) fold_group(std::integral_constant<int, 3>());
+            else if (left == 2u) fold_group(std::integral_constant<int, 2>());
+            else fold_group(std::integral_constant<int, 1>());
           }
         }
-        __syncthreads();
+        issue_round(r + kStages - 1);
+        {
+          const uint32_t xh = r + kHdrAhead;
+          if (desc_tid >= 0 && desc_tid < (int)B && xh < R && xh * B + desc_tid < S_tot) fetch_hdr(xh, (uint32_t)desc_tid);
+        }
+        cp_async_commit();
       }
       cp_async_wait<0>();
+      __syncthreads();
     }
     done += Wn;
   }

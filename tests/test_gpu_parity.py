@@ -151,7 +151,7 @@ def test_simulate_in_pieces_equals_one_call(cortex):
             assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(fold=1), dict(ring=2), dict(ring=2, fold=1, l2_persist=-1),
+@pytest.mark.parametrize("opts", [dict(), dict(fold=1), dict(ring=2, l2_persist=1), dict(ring=2, fold=1, l2_persist=-1),
                                   dict(mode=1, ring=2)])
 def test_bf16_weights_match_oracle_with_bf16_weights(cortex, opts):
     """BF16 storage with FP32 accumulation is deterministic: equal to the FP32 oracle run with the
@@ -167,8 +167,8 @@ def test_bf16_weights_match_oracle_with_bf16_weights(cortex, opts):
         st = net.stats()
     assert c6[3] == 88.0 and c6[4] == -440.0
     assert st["exact_fold"] == (0 if opts.get("fold") == 1 else 1)
-    if st["ring_in_smem"] == 0 and opts.get("l2_persist", 0) >= 0:
-        assert st["l2_persist_bytes"] > 0
+    if st["ring_in_smem"] == 0:
+        assert (st["l2_persist_bytes"] > 0) == (opts.get("l2_persist", 0) > 0)
     ref, os_, oi, _ = oracle_run(spec, seed, steps)
     assert len(os_) > 100
     assert first_mismatch(gs, gi, os_, oi) == -1
