@@ -137,8 +137,7 @@ typedef struct cortex_options {
                                         descriptors of the coming rounds while the delivery warps
                                         fold (warps_per_block stays the number of delivery warps, at
                                         most 15); -1 = off; 0 = auto: on when the ring is in global
-                                        memory and the fold is ordered, in persistent mode.  Same
-                                        results. */
+                                        memory, in persistent mode.  Same results. */
 } cortex_options;
 
 typedef struct cortex_stats_t {

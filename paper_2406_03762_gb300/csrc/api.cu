@@ -600,12 +600,13 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   const int nn = h->n_nets;
   std::vector<int> cw(nn), cm(nn);
   std::vector<size_t> per(nn);  // staging bytes per spike of a round (kStages rounds in flight)
-  // the helper warp (it builds the descriptors and the delivery warps' segment tables): as asked,
-  // else automatic for the persistent kernel with the ring in global memory and the ordered fold
+  // the helper warp (it fetches the piece headers and builds the descriptors while the others
+  // fold): as asked, else automatic for the persistent kernel with the ring in global memory (where
+  // it measured faster; with the ring in shared memory it measured slower)
   auto helper_for = [&](bool ring) {
     if (h->delivery != CORTEX_DELIVERY_RING || h->n_warps >= kMaxWarps) return false;
     if (o.helper_warp != 0) return o.helper_warp > 0;
-    return !h->no_auto_helper && h->mode == CORTEX_MODE_PERSISTENT && !ring && !h->exact;
+    return !h->no_auto_helper && h->mode == CORTEX_MODE_PERSISTENT && !ring;
   };
   auto layout = [&](int b, bool ring, size_t stage) {
     const NetDev& d = h->nets_h[b];
