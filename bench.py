@@ -66,6 +66,12 @@ def _peaks():
 def workload_config(cfg) -> dict:
     """The workload as both arms name it: what is simulated, not how."""
     spec = cfg["spec"]
+    if spec is None:  # the batch of uneven networks
+        from paper_2406_03762_gb300 import workloads as W
+        specs, _ = W.batch_specs()
+        return {"workload": cfg["name"], "n_nets": len(specs), "n_neurons": sum(x.n for x in specs),
+                "synapses": sum(x.n * x.k for x in specs), "weights": "f32", "dt_ms": specs[0].dt,
+                "l2": "inputs larger than L2 (records %.1f GB)" % (sum(x.n * x.k for x in specs) * 6 / 1e9)}
     return {"workload": cfg["name"], "n_neurons": spec.n, "k": spec.k, "synapses": spec.n * spec.k,
             "d_min": spec.d_min, "d_max": spec.d_max, "weights": "bf16" if spec.weight_dtype == 1 else "f32",
             "dt_ms": spec.dt, "l2": "inputs larger than L2 (records %.1f GB)" % (
@@ -250,10 +256,15 @@ def our_arm(args):
     cfg = _config(args.config)
     spec = cfg["spec"]
     seed = replica_seed(cfg["seed"], rank)
+    net_spec, net_seed = spec, seed
+    if spec is None:  # the batch of uneven networks (library's default plan; the form autotunes it)
+        specs, seeds = W.batch_specs()
+        net_spec, net_seed = specs, [replica_seed(x, rank) for x in seeds]
+        spec = specs[0]  # per-network values below (weight type, dt) are common to the batch
     stream = torch.cuda.Stream()
     opts = cortex.make_options(steps_per_launch=args.steps_per_launch, warps_per_block=args.warps,
                                delivery=args.delivery)
-    net = cortex.Network(spec, seed, opts, stream=stream)
+    net = cortex.Network(net_spec, net_seed, opts, stream=stream)
     st0 = net.stats()
 
     def barrier():
@@ -298,7 +309,7 @@ def our_arm(args):
     e2e_events = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        with cortex.Network(spec, seed, opts, stream=stream) as n2:
+        with cortex.Network(net_spec, net_seed, opts, stream=stream) as n2:
             n2.simulate(args.sim_steps)
             s_, i_ = n2.spikes()
             st2 = n2.stats()
@@ -381,11 +392,11 @@ FORMS = [
     ("bf16_delay_ordered", "c3", {"delivery": 1}, None),
 ]
 
-# ncu DRAM records per (configuration, delivery): bytes per event captured on a reduced network of
-# the same model (profiles/), valid while the kernel's code is the one captured
+# ncu DRAM records per (configuration, delivery): bytes per event captured at full size (profiles/),
+# valid while the kernel's code is the one captured
 TRAFFIC_RECORDS = {("c1", 0): "k_step_c1_traffic.json", ("c2", 0): "k_step_c2_traffic.json",
-                   ("c3", 0): "k_step_c3_traffic.json", ("c3", 1): "k_dstep_c3_traffic.json",
-                   ("c2", 1): "k_dstep_c2_traffic.json"}
+                   ("c3", 0): "k_step_c3_traffic.json", ("c4", 0): "k_step_c4_traffic.json",
+                   ("c3", 1): "k_dstep_c3_traffic.json", ("c2", 1): "k_dstep_c2_traffic.json"}
 
 
 def _form(cortex, W, name, kw, args, stream, peak, peak_kind, n_steps):
@@ -492,7 +503,7 @@ def kernel_digest(kernel: str = "k_step") -> str:
 
 def _traffic(events_per_launch, record):
     """DRAM bytes per launch from a committed ncu record (profiles/<record>: bytes per synaptic event
-    on a reduced network of the same model), scaled by the launch's events, if the kernel's code is
+    of the same workload at full size), scaled by the launch's events, if the kernel's code is
     unchanged since the capture; else None."""
     if record is None:
         return None
