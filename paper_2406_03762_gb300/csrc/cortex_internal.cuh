@@ -44,8 +44,7 @@ __host__ __device__ inline uint32_t hdr_end(const uint32_t* words, int w) {
 }
 constexpr int kSpikeBatch = 32;     // spikes staged per delivery round (at most)
 constexpr int kStages = 4;          // delivery rounds in flight per block
-constexpr int kHdrAhead = 2 * kStages - 1;        // headers are fetched this many rounds ahead
-constexpr int kHdrSlots = kHdrAhead - kStages + 1;  // rounds of headers held in shared memory
+constexpr int kHdrSlots = 4;       // rounds of fetched piece headers held in shared memory (two pairs)
 constexpr int kIdCap = 2048;        // spike ids of a window kept in shared memory
 constexpr int kMboxWords = 16;      // 64-bit words of a block's mailbox line (128 bytes)
 constexpr int kInlMax = 3 * (kMboxWords - 1);  // spike ids a mailbox line carries (one count word)

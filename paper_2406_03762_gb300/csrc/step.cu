@@ -29,18 +29,21 @@
 // other blocks), then the threads of the polls read the lines.
 //
 // Delivery runs in rounds of up to kSpikeBatch spikes (per network: as many as its staging
-// layout holds).  Headers (and row starts) are copied into
-// shared memory kHdrAhead rounds ahead; one lane per spike turns them into a piece descriptor
+// layout holds), taken in pairs behind one block barrier.  Headers (and row starts) are copied into
+// shared memory a pair ahead of their use; one lane per spike turns them into a piece descriptor
 // (global addresses and 16-byte chunk counts for the copy, spike-minor offsets and per-warp ends
-// for the fold); all warps stage the records of round r + kStages - 1 with 16-byte cp.async copies
-// (each spike has a fixed-size region of its slot), then fold round r.  So kStages - 1 rounds of
-// records are always in flight.
+// for the fold); all warps stage the records of the next pair with 16-byte cp.async copies (each
+// spike has a fixed-size region of its slot), then fold the current pair while those land.
 #include <type_traits>
 
 #include "cortex_internal.cuh"
 #include "step_common.cuh"
 
 namespace cortex {
+
+// delivery rounds whose descriptors are kept: the pair being folded, the pair being copied and the
+// pair being described
+constexpr uint32_t kDescSlots = 6;
 
 struct SmemLayout {
   uint32_t ring, sv, si, sr, thr, cnt, woffs, wcnt, wlist, ids, mbl, mbi, mbc, pk, hdr, desc, dsoa, perm, tags, stage, total;
@@ -87,10 +90,10 @@ __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window,
   o += align_to((uint32_t)(window * nt), 16);
   L.hdr = o;   // fetched headers: kHdrSlots rounds of (32-byte header, 8-byte row start, pad) per spike
   o += kHdrSlots * kSpikeBatch * 48;
-  L.desc = o;  // piece descriptors, kStages + 1 rounds: 32 bytes per spike (copy), then per round
-  o += (kStages + 1) * kSpikeBatch * 32;  //   u32 aux[spike] and u16 end[warp][spike] (fold; from the 12-bit fields)
+  L.desc = o;  // piece descriptors, kDescSlots rounds: 32 bytes per spike (copy), then per round
+  o += kDescSlots * kSpikeBatch * 32;  //   u32 aux[spike] and u16 end[warp][spike] (fold; from the 12-bit fields)
   L.dsoa = o;
-  o += (kStages + 1) * kSpikeBatch * (4 + 2 * kMaxWarps);
+  o += kDescSlots * kSpikeBatch * (4 + 2 * kMaxWarps);
   L.perm = o;
   o += kMaxWarps * 32;
   o = align_to(o, 16);
@@ -145,8 +148,9 @@ __device__ __forceinline__ void fold_n(float* ring, uint8_t* wtags, const uint32
 // neuron touched by two threads is an error).  Every ring cell a delivery warp writes is stamped
 // with the warp's id (block * 16 + warp + 1) in a global array laid out like the global ring; a cell
 // found stamped by another warp is counted (viol[0]) and the first one recorded (viol[1] = cell + 1).
-// Nothing traps: the host reads the counters after the launch.
-__device__ __forceinline__ void stamp_cell(const StepArgs& a, int64_t ring_base, uint32_t key, uint32_t writer) {
+// Nothing traps: the host reads the counters after the launch.  Out of line: debug mode only, and
+// the fold it sits in is inlined for every chunk of every group size.
+__device__ __noinline__ void stamp_cell(const StepArgs& a, int64_t ring_base, uint32_t key, uint32_t writer) {
   if (key == 0xffffffffu) return;
   const int64_t cell = ring_base + key;
   const uint32_t old = atomicCAS(a.stamps + cell, 0u, writer);
@@ -657,9 +661,9 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
       // weight chunks | meta chunks << 16.  For the fold (read by lane k of a warp, so stored spike-minor to keep
       // the lanes on distinct banks): aux[k] = weight offset | meta offset << 8 | emission slot <<
       // 16, and the header's end[w][k].
-      auto desc_slot = [&](uint32_t x) { return desc_s + (x % (kStages + 1)) * (2 * kSpikeBatch); };
+      auto desc_slot = [&](uint32_t x) { return desc_s + (x % kDescSlots) * (2 * kSpikeBatch); };
       auto aux_slot = [&](uint32_t x) {
-        return reinterpret_cast<uint32_t*>(dsoa_s + (x % (kStages + 1)) * kSpikeBatch * (4 + 2 * kMaxWarps));
+        return reinterpret_cast<uint32_t*>(dsoa_s + (x % kDescSlots) * kSpikeBatch * (4 + 2 * kMaxWarps));
       };
       auto ends_slot = [&](uint32_t x) { return reinterpret_cast<uint16_t*>(aux_slot(x) + kSpikeBatch); };
       auto store_desc = [&](uint32_t x) {
@@ -712,35 +716,34 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         }
       };
       const uint32_t lanes_lt = lanemask_lt();
-      // Pipeline (iteration r): wait until round r's copy group is complete (committed kStages - 1
-      // iterations earlier) and meet at the round's barrier; build the descriptors of round
-      // r + kStages from headers fetched kHdrAhead - kStages iterations earlier (whose groups are
-      // complete by then since kHdrAhead >= 2 kStages - 1); fold round r; then, without another
-      // barrier, issue the records of round r + kStages - 1 into the slot of round r - 1 (every
-      // warp finished folding round r - 1 before this round's barrier) and the headers of round
-      // r + kHdrAhead.  One barrier per round; the window's last folds meet the update at the
-      // barrier after the loop.
+      // Pipeline: rounds in pairs, one block barrier per pair.  Iteration of pair (r0, r0 + 1): wait
+      // for the thread's copies (the pair's records and the headers of rounds r0 + 4, r0 + 5, all
+      // issued in the previous iteration) and meet at the barrier; build the descriptors of rounds
+      // r0 + 4 and r0 + 5 and fetch the headers of rounds r0 + 6 and r0 + 7 (header slots of rounds
+      // r0 + 2 and r0 + 3, whose descriptors were built in the previous iteration); issue the
+      // records of rounds r0 + 2 and r0 + 3 into the staging slots of rounds r0 - 2 and r0 - 1, which
+      // every warp folded before this barrier; then fold rounds r0 and r0 + 1, during which those
+      // copies land.  Descriptor slots: six rounds (the pair being folded, the pair being copied,
+      // the pair being described).  The fold has one call site (code size: a second inlined copy of
+      // it measured slower), and the window's last folds meet the update at the barrier after the
+      // loop.
       if (R > 0) {
         // descriptors of the first kStages rounds (their headers were copied with the ids), then the
-        // headers of rounds kStages .. kHdrAhead - 1 and the records of the first kStages - 1 rounds
+        // headers of rounds 4 and 5 and the records of the first pair
         for (uint32_t x = (uint32_t)warp; x < min(R, (uint32_t)kStages); x += (uint32_t)n_warps) store_desc(x);
         __syncthreads();
-        for (uint32_t i = tid; i < (uint32_t)(kHdrAhead - kStages) * B; i += blockDim.x) {
-          const uint32_t x = kStages + i / B, k = i % B;
+        for (uint32_t i = tid; i < 2u * B; i += blockDim.x) {
+          const uint32_t x = 4u + i / B, k = i % B;
           if (x < R && x * B + k < S_tot) fetch_hdr(x, k);
         }
-        for (int x = 0; x < kStages - 1; ++x) {
-          issue_round((uint32_t)x);
-          cp_async_commit();
-        }
+        issue_round(0u);
+        issue_round(1u);
+        cp_async_commit();
       }
       const uint32_t wbase_t = (uint32_t)(warp * tw);
       const uint32_t writer = (uint32_t)(blk * kMaxWarps + warp) + 1u;  // ownership check: this warp's stamp
       uint8_t* wtags = kRingSmem ? tags : tags + (size_t)warp * kTagHash;
-      for (uint32_t r = 0; r < R; ++r) {
-        cp_async_wait<kStages - 2>();
-        __syncthreads();
-        if (desc_tid >= 0 && desc_tid < 32 && r + kStages < R) store_desc(r + kStages);  // the helper, else warp 0
+      auto fold_round = [&](const uint32_t r) {
 
         // ---- fold round r: each delivery warp, its target sub-range of every staged piece, in spike order
         if (warp < n_fold) {
@@ -842,20 +845,36 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
             }
             e += 32u * N;
           };
-          while (e < total) {
-            const uint32_t left = (total - e + 31u) >> 5;
-            if (left >= 4u) fold_group(std::integral_constant<int, 4>());
-            else if (left == 3u) fold_group(std::integral_constant<int, 3>());
-            else if (left == 2u) fold_group(std::integral_constant<int, 2>());
-            else fold_group(std::integral_constant<int, 1>());
+          if constexpr (kExact) {
+            // order-free adds: pairs of chunks (the second may be empty), one instantiation of the
+            // group (smaller code measured faster than groups of one to four here)
+            while (e < total) fold_group(std::integral_constant<int, 2>());
+          } else {
+            while (e < total) {
+              const uint32_t left = (total - e + 31u) >> 5;
+              if (left >= 4u) fold_group(std::integral_constant<int, 4>());
+              else if (left == 3u) fold_group(std::integral_constant<int, 3>());
+              else if (left == 2u) fold_group(std::integral_constant<int, 2>());
+              else fold_group(std::integral_constant<int, 1>());
+            }
           }
         }
-        issue_round(r + kStages - 1);
-        {
-          const uint32_t xh = r + kHdrAhead;
-          if (desc_tid >= 0 && desc_tid < (int)B && xh < R && xh * B + desc_tid < S_tot) fetch_hdr(xh, (uint32_t)desc_tid);
+      };
+      for (uint32_t r0 = 0; r0 < R; r0 += 2u) {
+        cp_async_wait<0>();
+        __syncthreads();
+        if (desc_tid >= 0 && desc_tid < 32) {  // the helper, else warp 0
+          if (r0 + 4u < R) store_desc(r0 + 4u);
+          if (r0 + 5u < R) store_desc(r0 + 5u);
         }
+        if (desc_tid >= 0 && desc_tid < (int)B)
+          for (uint32_t xh = r0 + 6u; xh < r0 + 8u; ++xh)
+            if (xh < R && xh * B + desc_tid < S_tot) fetch_hdr(xh, (uint32_t)desc_tid);
+        issue_round(r0 + 2u);
+        issue_round(r0 + 3u);
         cp_async_commit();
+#pragma unroll 1
+        for (uint32_t r = r0; r < min(r0 + 2u, R); ++r) fold_round(r);
       }
       cp_async_wait<0>();
       __syncthreads();

@@ -106,7 +106,24 @@ __device__ __forceinline__ float ring_read(const float* p) {
 //     unshared lanes, then the higher lanes add;
 //   - otherwise: unshared lanes at once, then the shared lanes one by one in lane order.
 // With hashed tags two lanes of different cells may be taken for a pair: they are then merely
-// ordered, which is always allowed.
+// ordered, which is always allowed.  The general case is rare and kept out of line
+// (fold_apply_serial): the fold is inlined into every chunk of every group size, and its code size
+// measured in the step time.
+template <bool kRingSmem>
+__device__ __noinline__ void fold_apply_serial(float* ring, uint32_t key, float w, uint32_t dup, int lane, bool red) {
+  const bool valid = key != 0xffffffffu;
+  const bool isdup = (dup >> lane) & 1u;
+  if (valid && !isdup) ring_add<kRingSmem>(ring, key, w, red);
+  __syncwarp();
+  uint32_t m = dup;
+  while (m) {
+    const int f = __ffs(m) - 1;
+    if (lane == f) ring_add<kRingSmem>(ring, key, w, red);
+    __syncwarp();
+    m &= m - 1u;
+  }
+}
+
 template <bool kRingSmem>
 __device__ __forceinline__ void fold_apply(float* ring, uint32_t key, float w, uint32_t t, uint32_t losers, int lane,
                                            bool red) {
@@ -129,15 +146,7 @@ __device__ __forceinline__ void fold_apply(float* ring, uint32_t key, float w, u
     __syncwarp();
     return;
   }
-  if (valid && !isdup) ring_add<kRingSmem>(ring, key, w, red);
-  __syncwarp();
-  uint32_t m = dup;
-  while (m) {
-    const int f = __ffs(m) - 1;
-    if (lane == f) ring_add<kRingSmem>(ring, key, w, red);
-    __syncwarp();
-    m &= m - 1u;
-  }
+  fold_apply_serial<kRingSmem>(ring, key, w, dup, lane, red);
 }
 
 // Fold one chunk: every lane writes its lane id into the tag of its cell and reads it back, which
