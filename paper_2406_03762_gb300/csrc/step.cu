@@ -170,8 +170,10 @@ template <bool kRingSmem, bool kBf16, bool kWide, bool kExact>
 __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_step(const StepArgs a) {
   constexpr uint32_t kWsz = kBf16 ? 2u : 4u;  // bytes per stored weight
   // neuron chunks per update iteration: a global ring is read from L2, so several reads are kept
-  // in flight; a shared ring is read with low latency and small per-warp ranges favour one
-  constexpr int kUpd = kRingSmem ? 1 : 4;
+  // in flight (8: one L2 round trip per step for about 250 targets per warp; measured 1% faster than
+  // 4 on the 500,000- and 1e6-neuron networks); a shared ring is read with low latency and small
+  // per-warp ranges favour one
+  constexpr int kUpd = kRingSmem ? 1 : 8;
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
   // delivery warps own the target sub-ranges of the layout; with a helper warp (the last one), that
