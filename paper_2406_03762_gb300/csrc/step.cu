@@ -94,8 +94,8 @@ __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window,
   o += kDescSlots * kSpikeBatch * 32;  //   u32 aux[spike] and u16 end[warp][spike] (fold; from the 12-bit fields)
   L.dsoa = o;
   o += kDescSlots * kSpikeBatch * (4 + 2 * kMaxWarps);
-  L.perm = o;
-  o += kMaxWarps * 32;
+  L.perm = o;  // per delivery warp, the compaction of the non-empty pieces of a round (two rounds)
+  o += kMaxWarps * 64;
   o = align_to(o, 16);
   L.tags = o;
   o += ring_smem ? align_to((uint32_t)(depth * nt), 16) : (uint32_t)(n_warps * kTagHash);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
   unsigned char* hdr_s = smem + L.hdr;
   uint4* desc_s = reinterpret_cast<uint4*>(smem + L.desc);
   unsigned char* dsoa_s = smem + L.dsoa;
-  uint8_t* perm = smem + L.perm + warp * 32;
+  uint8_t* perm = smem + L.perm + warp * 64;
   uint8_t* tags = smem + L.tags;
   unsigned char* stage = smem + L.stage;
 
@@ -745,121 +745,175 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
       const uint32_t wbase_t = (uint32_t)(warp * tw);
       const uint32_t writer = (uint32_t)(blk * kMaxWarps + warp) + 1u;  // ownership check: this warp's stamp
       uint8_t* wtags = kRingSmem ? tags : tags + (size_t)warp * kTagHash;
-      auto fold_round = [&](const uint32_t r) {
-
-        // ---- fold round r: each delivery warp, its target sub-range of every staged piece, in spike order
-        if (warp < n_fold) {
-          // the warp's segments (spikes with entries in its sub-range), in spike order: per lane,
-          // the first entry of segment `lane` in the warp's stream of the round, the staging
-          // addresses of entry 0 as if the segment started there, the emission slot + d_min
-          const uint32_t* aux_r = aux_slot(r);
-          const uint16_t* ends_r = ends_slot(r);
-          const uint32_t n = min(B, S_tot - r * B);
-          const uint32_t sbase = (r % kStages) * (B * cap);
-          uint32_t len_k = 0, wb_k = 0, mb_k = 0, sb_k = 0;
-          if ((uint32_t)lane < n) {
-            const uint32_t e1 = ends_r[warp * kSpikeBatch + lane];
-            const uint32_t e0 = warp ? ends_r[(warp - 1) * kSpikeBatch + lane] : 0u;
-            const uint32_t aux = aux_r[lane];
-            len_k = e1 - e0;
-            const uint32_t pk = sbase + (uint32_t)lane * cap;
-            wb_k = pk + (aux & 15u) + e0 * kWsz;
-            mb_k = pk + cap_w + ((aux >> 8) & 15u) + e0 * 2u;
-            sb_k = (aux >> 16) + (uint32_t)d_min;
+      // The chunks of one round for this delivery warp, given its segments: per lane, the first
+      // entry of segment `lane` in the warp's stream of the round (c_start), the staging addresses
+      // of entry 0 as if the segment started there (c_wadj, c_madj), the emission slot + d_min;
+      // n_ne segments, total entries.
+      auto fold_chunks = [&](const uint32_t c_start, const uint32_t c_wadj, const uint32_t c_madj, const uint32_t c_sb,
+                             const int n_ne, const uint32_t total) {
+        if (lane == 0) my_events += total;
+        int cur = -1;  // segment of the entry before the next chunk
+        // the warp's chunks of 32 entries, up to four at a time.  Keys (ring cells, 0xffffffff:
+        // no entry) and weights of all of a group's chunks are found step by step across the
+        // chunks (segment starts, segment of each lane's entry, its staging addresses, its
+        // record), so that the chunks' dependency chains overlap; then their ring updates run
+        // in chunk order.
+        uint32_t e = 0;
+        auto fold_group = [&](auto nc) {
+          constexpr int N = decltype(nc)::value;
+          uint32_t key[N], sm[N], wa[N], ma[N], sbv[N];
+          int sl[N];
+          float wv[N];
+#pragma unroll
+          for (int u = 0; u < N; ++u) {
+            const uint32_t cb = e + 32u * u;
+            sm[u] = __reduce_or_sync(0xffffffffu, (lane < n_ne && c_start - cb < 32u) ? (1u << (c_start - cb)) : 0u);
           }
-          // pieces in spike order; empty ones are dropped so that segment starts are distinct
-          const uint32_t ne = __ballot_sync(0xffffffffu, len_k > 0);
-          const int n_ne = __popc(ne);
-          uint32_t c_len = len_k, c_wb = wb_k, c_mb = mb_k, c_sb = sb_k;
-          if (ne != (0xffffffffu >> (32 - max(n_ne, 1))) || n_ne == 0) {
-            if (len_k > 0) perm[__popc(ne & lanes_lt)] = (uint8_t)lane;
-            __syncwarp();
-            const int src_lane = (lane < n_ne) ? (int)perm[lane] : 0;
-            c_len = __shfl_sync(0xffffffffu, len_k, src_lane);
-            c_wb = __shfl_sync(0xffffffffu, wb_k, src_lane);
-            c_mb = __shfl_sync(0xffffffffu, mb_k, src_lane);
-            c_sb = __shfl_sync(0xffffffffu, sb_k, src_lane);
-            if (lane >= n_ne) c_len = 0;
-            __syncwarp();
+#pragma unroll
+          for (int u = 0; u < N; ++u) {
+            sl[u] = (cur + __popc(sm[u] & (lanes_lt | (1u << lane)))) & 31;
+            cur += __popc(sm[u]);
           }
-          uint32_t c_end = c_len;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, c_end, o);
-            if (lane >= o) c_end += y;
+          for (int u = 0; u < N; ++u) wa[u] = __shfl_sync(0xffffffffu, c_wadj, sl[u]);
+#pragma unroll
+          for (int u = 0; u < N; ++u) ma[u] = __shfl_sync(0xffffffffu, c_madj, sl[u]);
+#pragma unroll
+          for (int u = 0; u < N; ++u) sbv[u] = __shfl_sync(0xffffffffu, c_sb, sl[u]);
+#pragma unroll
+          for (int u = 0; u < N; ++u) {
+            const uint32_t q = e + 32u * u + lane;
+            key[u] = 0xffffffffu;
+            wv[u] = 0.0f;
+            if (q < total) {
+              const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + ma[u] + 2u * q);
+              if constexpr (kBf16) wv[u] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + wa[u] + 2u * q));
+              else wv[u] = *reinterpret_cast<const float*>(stage + wa[u] + 4u * q);
+              uint32_t slot = sbv[u] + (meta & dmask);
+              if (slot >= (uint32_t)D) slot -= (uint32_t)D;
+              key[u] = slot * (uint32_t)nt + wbase_t + (meta >> dbits);
+            }
           }
-          const uint32_t c_start = c_end - c_len;
-          const uint32_t total = __shfl_sync(0xffffffffu, c_end, 31);
-          // staging addresses of entry q of a segment: base + q * size (q counts over the round)
-          const uint32_t c_wadj = c_wb - c_start * kWsz, c_madj = c_mb - c_start * 2u;
-          if (lane == 0) my_events += total;
-          int cur = -1;  // segment of the entry before the next chunk
-          // the warp's chunks of 32 entries, up to four at a time.  Keys (ring cells, 0xffffffff:
-          // no entry) and weights of all of a group's chunks are found step by step across the
-          // chunks (segment starts, segment of each lane's entry, its staging addresses, its
-          // record), so that the chunks' dependency chains overlap; then their ring updates run
-          // in chunk order.
-          uint32_t e = 0;
-          auto fold_group = [&](auto nc) {
-            constexpr int N = decltype(nc)::value;
-            uint32_t key[N], sm[N], wa[N], ma[N], sbv[N];
-            int sl[N];
-            float wv[N];
+          if (a.stamps != nullptr)
 #pragma unroll
-            for (int u = 0; u < N; ++u) {
-              const uint32_t cb = e + 32u * u;
-              sm[u] = __reduce_or_sync(0xffffffffu, (lane < n_ne && c_start - cb < 32u) ? (1u << (c_start - cb)) : 0u);
-            }
-#pragma unroll
-            for (int u = 0; u < N; ++u) {
-              sl[u] = (cur + __popc(sm[u] & (lanes_lt | (1u << lane)))) & 31;
-              cur += __popc(sm[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < N; ++u) wa[u] = __shfl_sync(0xffffffffu, c_wadj, sl[u]);
-#pragma unroll
-            for (int u = 0; u < N; ++u) ma[u] = __shfl_sync(0xffffffffu, c_madj, sl[u]);
-#pragma unroll
-            for (int u = 0; u < N; ++u) sbv[u] = __shfl_sync(0xffffffffu, c_sb, sl[u]);
-#pragma unroll
-            for (int u = 0; u < N; ++u) {
-              const uint32_t q = e + 32u * u + lane;
-              key[u] = 0xffffffffu;
-              wv[u] = 0.0f;
-              if (q < total) {
-                const uint32_t meta = *reinterpret_cast<const uint16_t*>(stage + ma[u] + 2u * q);
-                if constexpr (kBf16) wv[u] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage + wa[u] + 2u * q));
-                else wv[u] = *reinterpret_cast<const float*>(stage + wa[u] + 4u * q);
-                uint32_t slot = sbv[u] + (meta & dmask);
-                if (slot >= (uint32_t)D) slot -= (uint32_t)D;
-                key[u] = slot * (uint32_t)nt + wbase_t + (meta >> dbits);
-              }
-            }
-            if (a.stamps != nullptr)
-#pragma unroll
-              for (int u = 0; u < N; ++u) stamp_cell(a, wk.ring_base, key[u], writer);
-            if constexpr (kExact) {
-#pragma unroll
-              for (int u = 0; u < N; ++u)
-                if (key[u] != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key[u], wv[u]);
-            } else {
-              fold_n<kRingSmem, N>(ring, wtags, key, wv, lane, ring_red);
-            }
-            e += 32u * N;
-          };
+            for (int u = 0; u < N; ++u) stamp_cell(a, wk.ring_base, key[u], writer);
           if constexpr (kExact) {
-            // order-free adds: pairs of chunks (the second may be empty), one instantiation of the
-            // group (smaller code measured faster than groups of one to four here)
-            while (e < total) fold_group(std::integral_constant<int, 2>());
+#pragma unroll
+            for (int u = 0; u < N; ++u)
+              if (key[u] != 0xffffffffu) ring_add_exact<kRingSmem>(ring, key[u], wv[u]);
           } else {
-            while (e < total) {
-              const uint32_t left = (total - e + 31u) >> 5;
-              if (left >= 4u) fold_group(std::integral_constant<int, 4>());
-              else if (left == 3u) fold_group(std::integral_constant<int, 3>());
-              else if (left == 2u) fold_group(std::integral_constant<int, 2>());
-              else fold_group(std::integral_constant<int, 1>());
-            }
+            fold_n<kRingSmem, N>(ring, wtags, key, wv, lane, ring_red);
           }
+          e += 32u * N;
+        };
+        if constexpr (kExact) {
+          // order-free adds: pairs of chunks (the second may be empty), one instantiation of the
+          // group (smaller code measured faster than groups of one to four here)
+          while (e < total) fold_group(std::integral_constant<int, 2>());
+        } else {
+          while (e < total) {
+            const uint32_t left = (total - e + 31u) >> 5;
+            if (left >= 4u) fold_group(std::integral_constant<int, 4>());
+            else if (left == 3u) fold_group(std::integral_constant<int, 3>());
+            else if (left == 2u) fold_group(std::integral_constant<int, 2>());
+            else fold_group(std::integral_constant<int, 1>());
+          }
+        }
+      };
+      // the warp's segments of round r (spikes with entries in its sub-range), in spike order;
+      // empty pieces are dropped so that segment starts are distinct
+      auto segments_in = [&](const uint32_t r, uint32_t& len_k, uint32_t& wb_k, uint32_t& mb_k, uint32_t& sb_k) {
+        len_k = wb_k = mb_k = sb_k = 0u;
+        const uint32_t* aux_r = aux_slot(r);
+        const uint16_t* ends_r = ends_slot(r);
+        const uint32_t n = min(B, S_tot - r * B);
+        if ((uint32_t)lane < n) {
+          const uint32_t e1 = ends_r[warp * kSpikeBatch + lane];
+          const uint32_t e0 = warp ? ends_r[(warp - 1) * kSpikeBatch + lane] : 0u;
+          const uint32_t aux = aux_r[lane];
+          len_k = e1 - e0;
+          const uint32_t pk = (r % kStages) * (B * cap) + (uint32_t)lane * cap;
+          wb_k = pk + (aux & 15u) + e0 * kWsz;
+          mb_k = pk + cap_w + ((aux >> 8) & 15u) + e0 * 2u;
+          sb_k = (aux >> 16) + (uint32_t)d_min;
+        }
+      };
+      // ---- fold round r: each delivery warp, its target sub-range of every staged piece, in spike order
+      auto fold_round = [&](const uint32_t r) {
+        if (warp >= n_fold) return;
+        uint32_t len_k, wb_k, mb_k, sb_k;
+        segments_in(r, len_k, wb_k, mb_k, sb_k);
+        const uint32_t ne = __ballot_sync(0xffffffffu, len_k > 0);
+        const int n_ne = __popc(ne);
+        uint32_t c_len = len_k, c_wb = wb_k, c_mb = mb_k, c_sb = sb_k;
+        if (ne != (0xffffffffu >> (32 - max(n_ne, 1))) || n_ne == 0) {
+          if (len_k > 0) perm[__popc(ne & lanes_lt)] = (uint8_t)lane;
+          __syncwarp();
+          const int src_lane = (lane < n_ne) ? (int)perm[lane] : 0;
+          c_len = __shfl_sync(0xffffffffu, len_k, src_lane);
+          c_wb = __shfl_sync(0xffffffffu, wb_k, src_lane);
+          c_mb = __shfl_sync(0xffffffffu, mb_k, src_lane);
+          c_sb = __shfl_sync(0xffffffffu, sb_k, src_lane);
+          if (lane >= n_ne) c_len = 0;
+          __syncwarp();
+        }
+        uint32_t c_end = c_len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, c_end, o);
+          if (lane >= o) c_end += y;
+        }
+        const uint32_t c_start = c_end - c_len;
+        fold_chunks(c_start, c_wb - c_start * kWsz, c_mb - c_start * 2u, c_sb, n_ne, __shfl_sync(0xffffffffu, c_end, 31));
+      };
+      // ---- fold rounds r0 and r0 + 1 with the two rounds' segment setups side by side (their chains
+      // overlap), then each round's chunks (the ring in global memory with the ordered fold, where it
+      // measured faster than one round at a time)
+      auto fold_pair = [&](const uint32_t r0) {
+        if (warp >= n_fold) return;
+        const uint32_t nr = min(2u, R - r0);
+        uint32_t len_k[2], wb_k[2], mb_k[2], sb_k[2], ne[2];
+        int nne[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          len_k[k] = wb_k[k] = mb_k[k] = sb_k[k] = 0u;
+          if ((uint32_t)k < nr) segments_in(r0 + (uint32_t)k, len_k[k], wb_k[k], mb_k[k], sb_k[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          ne[k] = __ballot_sync(0xffffffffu, len_k[k] > 0);
+          nne[k] = __popc(ne[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (len_k[k] > 0) perm[k * 32 + __popc(ne[k] & lanes_lt)] = (uint8_t)lane;
+        __syncwarp();
+        uint32_t c_len[2], c_wb[2], c_mb[2], c_sbk[2], c_end[2], tot[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int src_lane = (lane < nne[k]) ? (int)perm[k * 32 + lane] : 0;
+          c_len[k] = __shfl_sync(0xffffffffu, len_k[k], src_lane);
+          c_wb[k] = __shfl_sync(0xffffffffu, wb_k[k], src_lane);
+          c_mb[k] = __shfl_sync(0xffffffffu, mb_k[k], src_lane);
+          c_sbk[k] = __shfl_sync(0xffffffffu, sb_k[k], src_lane);
+          if (lane >= nne[k]) c_len[k] = 0;
+          c_end[k] = c_len[k];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, c_end[k], o);
+            if (lane >= o) c_end[k] += y;
+          }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) tot[k] = __shfl_sync(0xffffffffu, c_end[k], 31);
+#pragma unroll 1
+        for (uint32_t k = 0; k < nr; ++k) {
+          const uint32_t c_start = k ? c_end[1] - c_len[1] : c_end[0] - c_len[0];
+          fold_chunks(c_start, (k ? c_wb[1] : c_wb[0]) - c_start * kWsz, (k ? c_mb[1] : c_mb[0]) - c_start * 2u,
+                      k ? c_sbk[1] : c_sbk[0], k ? nne[1] : nne[0], k ? tot[1] : tot[0]);
         }
       };
       for (uint32_t r0 = 0; r0 < R; r0 += 2u) {
@@ -875,8 +929,12 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
         issue_round(r0 + 2u);
         issue_round(r0 + 3u);
         cp_async_commit();
+        if constexpr (!kRingSmem && !kExact) {
+          fold_pair(r0);
+        } else {
 #pragma unroll 1
-        for (uint32_t r = r0; r < min(r0 + 2u, R); ++r) fold_round(r);
+          for (uint32_t r = r0; r < min(r0 + 2u, R); ++r) fold_round(r);
+        }
       }
       cp_async_wait<0>();
       __syncthreads();
