@@ -86,6 +86,7 @@ struct cortex_net {
   bool exact = false;     // every partial sum of a ring cell is exact: order-free adds
   bool helper_warp = false;  // ring kernel: one more warp per block builds the piece descriptors
   bool no_auto_helper = false;  // the automatic helper warp was dropped (blocks not co-resident)
+  cortex_options build_opts = {};  // the build's options (a later switch to the ordered fold redoes the layout)
   int e_min = 0;          // exact: every weight is an integer multiple of 2^e_min
   double exact_bound = 0; // exact: largest |partial sum| of a cell, in units of 2^e_min
   cudaAccessPolicyWindow apw = {};  // the global ring, persisting in L2 (num_bytes 0: none)
@@ -272,7 +273,7 @@ int64_t max_block_targets(const cortex_params& p, int wsz, int n_warps, size_t s
     const double lam = (double)t * (double)k / (double)n;
     int cw = 0, cm = 0;
     step_staging_caps((int)std::ceil(lam + 6.0 * std::sqrt(lam) + 16.0), wsz, &cw, &cm);
-    const size_t fixed = step_smem_bytes((int)t, p.d_max + 1, p.d_min + 1, (int)ceil_div(n, t), false, 0, n_warps);
+    const size_t fixed = step_smem_bytes((int)t, p.d_max + 1, p.d_min + 1, (int)ceil_div(n, t), false, 0, n_warps, true);
     return fixed + (size_t)2 * kStages * (cw + cm) <= smem_cap;
   };
   int64_t lo = std::min<int64_t>(n, 32ll * n_warps), hi = std::min<int64_t>(n, 65535);
@@ -610,7 +611,8 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   };
   auto layout = [&](int b, bool ring, size_t stage) {
     const NetDev& d = h->nets_h[b];
-    return step_smem_bytes(h->work_h[d.first_block].nt, d.depth, d.window, d.n_blocks, ring, (int)stage, h->n_warps);
+    return step_smem_bytes(h->work_h[d.first_block].nt, d.depth, d.window, d.n_blocks, ring, (int)stage, h->n_warps,
+                           !h->exact);
   };
   auto room = [&](int b, bool ring) -> size_t {  // staging bytes that fit next to the rest
     const size_t fixed = layout(b, ring, 0);
@@ -664,6 +666,20 @@ int choose_stage_and_ring(cortex_net* h, const cortex_options& o) {
   CUDA_TRY(cudaMemcpyAsync(h->nets_d, h->nets_h.data(), sizeof(NetDev) * nn, cudaMemcpyHostToDevice, h->stream));
   h->h2d_bytes += (int64_t)(sizeof(NetDev) * nn);
   return CORTEX_OK;
+}
+
+// The layout again, after the handle switched from the order-free to the ordered fold (its shared
+// memory then holds the duplicate-detection tags): stage, ring placement and helper warp as at the
+// build, and split launches if the persistent kernel's blocks are no longer co-resident.
+int relayout_for_fold(cortex_net* h) {
+  int rc = choose_stage_and_ring(h, h->build_opts);
+  if (rc != CORTEX_OK) return rc;
+  if (h->mode == CORTEX_MODE_PERSISTENT && h->delivery == CORTEX_DELIVERY_RING &&
+      step_occupancy(h->threads, h->smem, h->ring_smem) * h->n_sm < h->n_blocks) {
+    h->mode = CORTEX_MODE_SPLIT;
+    rc = choose_stage_and_ring(h, h->build_opts);
+  }
+  return rc;
 }
 
 }  // namespace
@@ -722,6 +738,7 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     return rc;
   };
   h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->build_opts = o;
   if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(CORTEX_ERR_UNSUPPORTED, "no CUDA device"));
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(fail(CORTEX_ERR_CUDA, "device properties"));
@@ -1398,6 +1415,10 @@ int cortex_set_state(cortex_net* h, int32_t net_idx, const float* v, const float
       if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
+      }
+      if (h->delivery == CORTEX_DELIVERY_RING) {
+        const int rc = relayout_for_fold(h);
+        if (rc != CORTEX_OK) return rc;
       }
     }
   }

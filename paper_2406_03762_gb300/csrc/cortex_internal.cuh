@@ -287,7 +287,8 @@ cudaError_t launch_step(const StepArgs& a, int grid, int threads, size_t smem, b
 cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStream_t s);
 // dynamic shared memory of a block of a network: nt targets per block (its largest block),
 // ring depth, window steps, nb blocks, staging bytes
-size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes, int n_warps);
+size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes, int n_warps,
+                       bool ordered);
 void step_staging_caps(int max_seg_len, int wsz, int* cap_w, int* cap_m);
 cudaError_t step_kernel_attributes(size_t smem);
 int step_occupancy(int threads, size_t smem, bool ring_smem);

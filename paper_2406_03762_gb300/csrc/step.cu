@@ -52,8 +52,9 @@ struct SmemLayout {
 __host__ __device__ inline uint32_t align_to(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 
+// ordered: the fold orders equal cells (duplicate-detection tags); the order-free fold has none
 __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window, int nb, bool ring_smem,
-                                                  int stage_bytes, int n_warps) {
+                                                  int stage_bytes, int n_warps, bool ordered) {
   SmemLayout L;
   uint32_t o = 0;
   L.ring = o;
@@ -98,7 +99,7 @@ __host__ __device__ inline SmemLayout make_layout(int nt, int depth, int window,
   o += kMaxWarps * 64;
   o = align_to(o, 16);
   L.tags = o;
-  o += ring_smem ? align_to((uint32_t)(depth * nt), 16) : (uint32_t)(n_warps * kTagHash);
+  o += !ordered ? 0u : ring_smem ? align_to((uint32_t)(depth * nt), 16) : (uint32_t)(n_warps * kTagHash);
   o = align_to(o, 128);
   L.mbl = o;   // mailbox lines read at the barrier: one per block of the network
   o += (uint32_t)(nb * kMboxWords * 8);
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
   const uint32_t B = (uint32_t)ndg.batch, cap_w = (uint32_t)ndg.cap_w, cap = (uint32_t)(ndg.cap_w + ndg.cap_m);
 
   // the network's own layout (its blocks' targets, depth, window and block count)
-  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes, n_fold);
+  const SmemLayout L = make_layout(tb_full, D, window, nb, kRingSmem, ndg.stage_bytes, n_fold, !kExact);
   float* ring_s = reinterpret_cast<float*>(smem + L.ring);
   float* sV = reinterpret_cast<float*>(smem + L.sv);
   float* sI = reinterpret_cast<float*>(smem + L.si);
@@ -1035,8 +1036,9 @@ cudaError_t launch_advance_split(const StepArgs& a, int n_nets, int wn, cudaStre
   return cudaGetLastError();
 }
 
-size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes, int n_warps) {
-  return make_layout(nt, depth, window, nb, ring_smem, stage_bytes, n_warps).total;
+size_t step_smem_bytes(int nt, int depth, int window, int nb, bool ring_smem, int stage_bytes, int n_warps,
+                       bool ordered) {
+  return make_layout(nt, depth, window, nb, ring_smem, stage_bytes, n_warps, ordered).total;
 }
 
 // staging bytes per spike: a segment of up to max_seg_len records, widened to 16-byte boundaries
