@@ -661,9 +661,9 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
       };
       // Descriptors of round x, built by the 32 lanes of one warp (lane k: spike k of the round).
       // For the copy: [0] 16-byte-aligned global addresses of the weight and meta pieces, [1].x
-      // weight chunks | meta chunks << 16.  For the fold (read by lane k of a warp, so stored spike-minor to keep
-      // the lanes on distinct banks): aux[k] = weight offset | meta offset << 8 | emission slot <<
-      // 16, and the header's end[w][k].
+      // weight chunks | meta chunks << 16.  For the fold (read by lane k of a warp, so stored
+      // spike-minor to keep the lanes on distinct banks): aux[k] = weight offset | meta offset << 8 |
+      // emission slot << 16, and the header's end[w][k].
       auto desc_slot = [&](uint32_t x) { return desc_s + (x % kDescSlots) * (2 * kSpikeBatch); };
       auto aux_slot = [&](uint32_t x) {
         return reinterpret_cast<uint32_t*>(dsoa_s + (x % kDescSlots) * kSpikeBatch * (4 + 2 * kMaxWarps));
