@@ -188,10 +188,12 @@ def test_exact_fold_is_refused_when_sums_can_round(cortex):
         assert net.stats()["exact_fold"] == 0
 
 
-def test_restore_of_a_ring_off_the_weight_grid_keeps_results(cortex):
+@pytest.mark.parametrize("opts", [dict(), dict(ring=2)])
+def test_restore_of_a_ring_off_the_weight_grid_keeps_results(cortex, opts):
     """A restored ring whose values are not sums of the network's weights (here 0.1 pA) cannot use
-    the order-free fold: the handle returns to the ordered fold and still equals the oracle
-    started from the same state."""
+    the order-free fold: the handle returns to the ordered fold, whose shared-memory layout (with
+    the duplicate-detection tags) it recomputes, and still equals the oracle started from the same
+    state; with the ring in shared memory and in global memory."""
     spec, seed = SPECS[2], 99
     ref = orc.Network(oracle_params(spec), seed)
     ref.simulate(100)
@@ -202,10 +204,13 @@ def test_restore_of_a_ring_off_the_weight_grid_keeps_results(cortex):
     ref.simulate(300)
     s_all, i_all = ref.raster()
     keep = s_all >= 100
-    with cortex.Network(spec, seed) as net:
+    with cortex.Network(spec, seed, cortex.make_options(**opts)) as net:
         assert net.stats()["exact_fold"] == 1
         net.set_state(0, v=v.astype(np.float32), i_syn=c.astype(np.float32), refr=r, ring=ring.astype(np.float32))
-        assert net.stats()["exact_fold"] == 0
+        st = net.stats()
+        assert st["exact_fold"] == 0
+        if opts.get("ring") == 2:
+            assert st["ring_in_smem"] == 0
         net.set_step(100)
         net.simulate(300)
         gs, gi = net.spikes()
