@@ -100,3 +100,17 @@ def test_bench_form_line_without_gpu():
     assert out["dtype"] == "bf16" and abs(out["rtf"] - 0.605) < 1e-9
     assert abs(r["achieved"] - 5_818_217 * 1000 * 5 / 0.0605e-3 / 1e9 / 1000) < 1e-6 * r["achieved"]
     assert out["delivery"] == "ring" and out["exact_fold"] == 1
+
+
+def test_batch_workload_is_described_without_a_single_spec():
+    """The 64-network batch has no single network spec: the bench names it by its sizes, summed
+    over the batch, and every form's configuration has a traffic record at full size."""
+    from paper_2406_03762_gb300 import workloads as W
+    cfg = W.CONFIGS["c4"]
+    specs, seeds = W.batch_specs()
+    c = bench.workload_config(cfg)
+    assert c["workload"] == cfg["name"] and c["n_nets"] == len(specs) == len(seeds) == 64
+    assert c["n_neurons"] == sum(s.n for s in specs)
+    assert c["synapses"] == sum(s.n * s.k for s in specs)
+    for key, name, kw, _ in bench.FORMS:
+        assert (name, kw.get("delivery", 0)) in bench.TRAFFIC_RECORDS, key
