@@ -248,6 +248,57 @@ cudaError_t launch_build_fill_net(const NetDev* nets_dev, int net_idx, int32_t n
 constexpr int kSegCap = 2048;  // keys sorted in shared memory per warp
 static_assert(kSegCap <= (int)kMaxPiece, "piece ends are 12-bit header fields");
 
+// Bitonic sort, ascending, of the 32 E keys of a warp held in registers: key v[e] of lane l has
+// index l + 32 e.  Compare-exchange partners at distance jj < 32 are in lane l ^ jj (shuffle), at
+// distance >= 32 in the same lane; the result is the sorted sequence in the same index order.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(uint32_t (&v)[E], int lane) {
+  constexpr int P = 32 * E;
+#pragma unroll
+  for (int kk = 2; kk <= P; kk <<= 1) {
+#pragma unroll
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      if (jj >= 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int pe = e ^ (jj >> 5);
+          if (pe > e) {
+            const bool up = (((uint32_t)lane + 32u * (uint32_t)e) & (uint32_t)kk) == 0u;
+            const uint32_t x = v[e], y = v[pe];
+            if ((x > y) == up) {
+              v[e] = y;
+              v[pe] = x;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t y = __shfl_xor_sync(0xffffffffu, v[e], jj);
+          const bool up = (((uint32_t)lane + 32u * (uint32_t)e) & (uint32_t)kk) == 0u;
+          const bool lower = (lane & jj) == 0;
+          v[e] = (lower == up) ? min(v[e], y) : max(v[e], y);
+        }
+      }
+    }
+  }
+}
+
+// keys [key0, key0 + len) sorted into buf[0, len) by one warp in registers (len <= 32 E)
+template <int E>
+__device__ __forceinline__ void warp_sort_keys(const uint32_t* __restrict__ keys, int64_t key0, uint32_t len,
+                                               uint32_t* buf, int lane) {
+  uint32_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t q = (uint32_t)lane + 32u * (uint32_t)e;
+    v[e] = q < len ? keys[key0 + q] : 0xffffffffu;
+  }
+  warp_bitonic_sort<E>(v, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) buf[(uint32_t)lane + 32u * (uint32_t)e] = v[e];
+}
+
 __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ nets, const BlockWork* __restrict__ work,
                                                   int net_idx, int first_group, int n_groups, int n_dw,
                                                   const uint32_t* __restrict__ cnt,
@@ -286,25 +337,34 @@ __global__ void __launch_bounds__(256) k_finalize(const NetDev* __restrict__ net
     if (lane == 0 && len) atomicMax(max_seg, len);
     uint32_t p2 = 32;
     while (p2 < len) p2 <<= 1;
-    for (uint32_t q = lane; q < p2; q += 32) buf[q] = (q < len) ? keys[key0 + q] : 0xffffffffu;
-    __syncwarp();
-    // bitonic sort, ascending: (local target, draw)
-    for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
-      for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (uint32_t q = lane; q < p2; q += 32) {
-          const uint32_t l = q ^ jj;
-          if (l > q) {
-            const uint32_t x = buf[q], y = buf[l];
-            const bool up = (q & kk) == 0;
-            if ((x > y) == up) {
-              buf[q] = y;
-              buf[l] = x;
+    // sort ascending by (local target, draw): in registers up to 128 keys, else in shared memory
+    if (p2 <= 32) {
+      warp_sort_keys<1>(keys, key0, len, buf, lane);
+    } else if (p2 <= 64) {
+      warp_sort_keys<2>(keys, key0, len, buf, lane);
+    } else if (p2 <= 128) {
+      warp_sort_keys<4>(keys, key0, len, buf, lane);
+    } else {
+      for (uint32_t q = lane; q < p2; q += 32) buf[q] = (q < len) ? keys[key0 + q] : 0xffffffffu;
+      __syncwarp();
+      for (uint32_t kk = 2; kk <= p2; kk <<= 1) {
+        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+          for (uint32_t q = lane; q < p2; q += 32) {
+            const uint32_t l = q ^ jj;
+            if (l > q) {
+              const uint32_t x = buf[q], y = buf[l];
+              const bool up = (q & kk) == 0;
+              if ((x > y) == up) {
+                buf[q] = y;
+                buf[l] = x;
+              }
             }
           }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
+    __syncwarp();
     // the block's piece of the source's row (CSR by source, blocks in ascending order)
     const uint32_t piece = off_all[(int64_t)(first_group + g) * n + src];
     const int64_t r0 = rec_net + (int64_t)row_base[row_off + src] + piece;
