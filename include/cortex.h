@@ -275,9 +275,12 @@ int cortex_get_ring(cortex_net* net, int32_t net_idx, float* ring);
  * connectivity and the counter-based Poisson drive.  So a handle built from the same params and
  * seeds, given the state of every network and the step (cortex_set_step), continues a
  * checkpointed simulation bit for bit (Sec. II-B loop).  The recorded raster and the counters
- * are not part of the state.  Errors: CORTEX_ERR_ARG (index, or a refractory count outside
- * 0..n_ref; nothing is changed), CORTEX_ERR_TIMEOUT (an earlier device wait of the handle timed
- * out), CORTEX_ERR_CUDA. */
+ * are not part of the state.  A ring whose values are not sums of the network's weights on the
+ * grid that made the order-free fold exact (exact_fold in cortex_stats) returns the handle to
+ * the ordered fold, with a new shared-memory layout (same results).  Errors: CORTEX_ERR_ARG
+ * (index, or a refractory count outside 0..n_ref; nothing is changed), CORTEX_ERR_TIMEOUT (an
+ * earlier device wait of the handle timed out), CORTEX_ERR_UNSUPPORTED (the ordered fold's layout
+ * does not fit; the handle then refuses cortex_simulate and cortex_deliver), CORTEX_ERR_CUDA. */
 int cortex_set_state(cortex_net* net, int32_t net_idx, const float* v, const float* i_syn,
                      const int32_t* refr, const float* ring);
 

@@ -116,6 +116,7 @@ struct cortex_net {
   long long timeout_ns = 2000000000ll;
   int32_t withhold_block = -1;
   bool timed_out = false;  // a device wait gave up: the barrier epochs are inconsistent
+  bool no_layout = false;  // the switch to the ordered fold found no shared-memory layout: no launches
   std::vector<uint32_t> max_seg_len;  // longest (source, block) piece of each network
   size_t smem_cap = 0;                 // dynamic shared memory a block may use
   // bookkeeping
@@ -1213,6 +1214,8 @@ int cortex_simulate(cortex_net* h, int64_t n_steps) {
   NvtxRange nvtx_range("cortex_simulate");
   if (!h || n_steps < 0) return fail(CORTEX_ERR_ARG, "cortex_simulate: handle / n_steps");
   if (h->timed_out) return fail(CORTEX_ERR_TIMEOUT, "cortex_simulate: an earlier device wait timed out; free the handle");
+  if (h->no_layout)
+    return fail(CORTEX_ERR_UNSUPPORTED, "cortex_simulate: the restored ring needs the ordered fold, whose layout does not fit");
   unsigned long long ev_before = 0;
   {
     std::vector<unsigned long long> e(h->n_nets);
@@ -1418,7 +1421,10 @@ int cortex_set_state(cortex_net* h, int32_t net_idx, const float* v, const float
       }
       if (h->delivery == CORTEX_DELIVERY_RING) {
         const int rc = relayout_for_fold(h);
-        if (rc != CORTEX_OK) return rc;
+        if (rc != CORTEX_OK) {
+          h->no_layout = true;  // the order-free layout holds no tags for the ordered fold
+          return rc;
+        }
       }
     }
   }
@@ -1530,6 +1536,8 @@ int cortex_deliver(cortex_net* h, int32_t net_idx, const int32_t* ids, int64_t n
     return fail(CORTEX_ERR_ARG, "cortex_deliver: arguments");
   if (h->delivery == CORTEX_DELIVERY_DELAY)
     return fail(CORTEX_ERR_UNSUPPORTED, "cortex_deliver: measures the ring delivery only");
+  if (h->no_layout)
+    return fail(CORTEX_ERR_UNSUPPORTED, "cortex_deliver: the restored ring needs the ordered fold, whose layout does not fit");
   const NetDev& d = h->nets_h[net_idx];
   std::vector<int32_t> v(ids, ids + n);
   for (int32_t x : v)
