@@ -140,16 +140,22 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"cortex_clocks_{os.getpid()}_{id(self)}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"cortex_clocks_{os.getpid()}_{id(self)}.csv")
         self.t0 = self.t1 = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            with open(self.path, "w") as out:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                     "-lms", "20"], stdout=out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            try:
+                os.remove(self.path)  # no sampler on this machine: leave nothing behind
+            except OSError:
+                pass
             return self
         # wait (at most 3 s) for the first sample so that sampling covers the timed region
         t_end = time.time() + 3.0
