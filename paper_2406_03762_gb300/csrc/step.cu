@@ -453,12 +453,14 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
           else st_relaxed_u64(dst, tag | pay);
         }
         // L2 prefetch of the spiking rows (every block of the network reads them after the
-        // barrier): the header row and the record rows of the window's first spikes
+        // barrier): the header row, and with the ring in shared memory the record rows of the
+        // window's first spikes (with a ring in global memory, the burst of record rows evicted ring
+        // lines from L2 and measured slower: 1e6 neurons 6%, 500,000 neurons 1.7%)
         const int pq = tid - (int)(blockDim.x - kInlMax);
         if (pq >= 0 && (uint32_t)pq < nin) {
           const uint32_t id = (uint32_t)wk.t0 + mbi[pq];
           prefetch_l2_bulk(a.hdr + 2 * (hdr_net + (int64_t)id * nb), (uint32_t)nb * 32u);
-          if ((int)id + 1 < ndg.n) {
+          if (kRingSmem && (int)id + 1 < ndg.n) {
             const unsigned long long r0 = (unsigned long long)rec_net + __ldg(a.row_base + row_off + id);
             const unsigned long long r1 = (unsigned long long)rec_net + __ldg(a.row_base + row_off + id + 1);
             const unsigned long long spans[2][2] = {{r0 * kWsz, r1 * kWsz}, {r0 * 2ull, r1 * 2ull}};
