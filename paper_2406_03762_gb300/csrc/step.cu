@@ -24,8 +24,8 @@
 //
 // Publication and barrier: each block writes one 128-byte mailbox line per window whose 64-bit
 // words all carry the window's tag (step counts, then up to 45 spike ids), and bulk-prefetches
-// the rows of its spiking neurons into L2; reading every line of the network with the tag is the
-// barrier.  Every thread first makes the next window's Poisson draws (they need nothing from the
+// into L2 the header rows of its first spiking neurons (with the ring in shared memory, their record
+// rows too); reading every line of the network with the tag is the barrier.  Every thread first makes the next window's Poisson draws (they need nothing from the
 // other blocks), then the threads of the polls read the lines.
 //
 // Delivery runs in rounds of up to kSpikeBatch spikes (per network: as many as its staging
@@ -350,56 +350,56 @@ __global__ void __launch_bounds__((kWide ? kMaxWarps : kNarrowWarps) * 32, 1) k_
             cw += __popc(bal);
           }
         } else {
-        for (int c = lo; c < hi; c += kUpd * 32) {
-          // kUpd 32-neuron chunks: their loads are issued together, then updated, then compacted
-          // in ascending order
-          float v[kUpd], cur[kUpd], in[kUpd];
-          int32_t r[kUpd];
-          int kp[kUpd];
+          for (int c = lo; c < hi; c += kUpd * 32) {
+            // kUpd 32-neuron chunks: their loads are issued together, then updated, then compacted
+            // in ascending order
+            float v[kUpd], cur[kUpd], in[kUpd];
+            int32_t r[kUpd];
+            int kp[kUpd];
 #pragma unroll
-          for (int u = 0; u < kUpd; ++u) {
-            const int j = c + 32 * u + lane;
-            in[u] = 0.0f;
-            kp[u] = 0;
-            if (j < hi) {
-              v[u] = sV[j];
-              cur[u] = sI[j];
-              r[u] = sR[j];
-              if (!defer || prev) in[u] = ring_read<kRingSmem>(rs + j);
-              if (defer && prev) kp[u] = pk[ws * nt + j];
-            }
-          }
-          bool spk[kUpd];
-#pragma unroll
-          for (int u = 0; u < kUpd; ++u) {
-            const int j = c + 32 * u + lane;
-            spk[u] = false;
-            if (j < hi) {
-              if (defer) {
-                if (prev) {
-                  rs[j] = 0.0f;
-                  i_half_k(cur[u], in[u], kp[u], nd);
-                }
-                spk[u] = v_half(v[u], cur[u], r[u], nd);
-              } else {
-                rs[j] = 0.0f;
-                const uint32_t gi = (uint32_t)(wk.t0 + j);
-                const uint4 rr = philox4x32_10(make_uint4(gi >> 2, tu, kStreamPoisson, 0u), seed_lo, seed_hi);
-                spk[u] = v_half(v[u], cur[u], r[u], nd);
-                i_half(cur[u], in[u], philox_word(rr, gi & 3u), nd, thr);
+            for (int u = 0; u < kUpd; ++u) {
+              const int j = c + 32 * u + lane;
+              in[u] = 0.0f;
+              kp[u] = 0;
+              if (j < hi) {
+                v[u] = sV[j];
+                cur[u] = sI[j];
+                r[u] = sR[j];
+                if (!defer || prev) in[u] = ring_read<kRingSmem>(rs + j);
+                if (defer && prev) kp[u] = pk[ws * nt + j];
               }
-              sV[j] = v[u];
-              sI[j] = cur[u];
-              sR[j] = (RefT)r[u];
+            }
+            bool spk[kUpd];
+#pragma unroll
+            for (int u = 0; u < kUpd; ++u) {
+              const int j = c + 32 * u + lane;
+              spk[u] = false;
+              if (j < hi) {
+                if (defer) {
+                  if (prev) {
+                    rs[j] = 0.0f;
+                    i_half_k(cur[u], in[u], kp[u], nd);
+                  }
+                  spk[u] = v_half(v[u], cur[u], r[u], nd);
+                } else {
+                  rs[j] = 0.0f;
+                  const uint32_t gi = (uint32_t)(wk.t0 + j);
+                  const uint4 rr = philox4x32_10(make_uint4(gi >> 2, tu, kStreamPoisson, 0u), seed_lo, seed_hi);
+                  spk[u] = v_half(v[u], cur[u], r[u], nd);
+                  i_half(cur[u], in[u], philox_word(rr, gi & 3u), nd, thr);
+                }
+                sV[j] = v[u];
+                sI[j] = cur[u];
+                sR[j] = (RefT)r[u];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < kUpd; ++u) {
+              const uint32_t bal = __ballot_sync(0xffffffffu, spk[u]);
+              if (spk[u]) wlist[lo + cw + __popc(bal & lanemask_lt())] = (ListT)(c + 32 * u + lane);
+              cw += __popc(bal);
             }
           }
-#pragma unroll
-          for (int u = 0; u < kUpd; ++u) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, spk[u]);
-            if (spk[u]) wlist[lo + cw + __popc(bal & lanemask_lt())] = (ListT)(c + 32 * u + lane);
-            cw += __popc(bal);
-          }
-        }
         }
         if (lane == 0) wcnt[warp] = cw;
         __syncthreads();
