@@ -930,10 +930,16 @@ int cortex_build_batch(const cortex_params* params, const uint64_t* seeds, int32
     rc = build_network(h, b, tb);
     if (rc != CORTEX_OK) return bail(rc);
     TRY(launch_init_state(&h->nets_h[b], h->nets_d, b, h->V, h->I, h->R, s), "init state");
-    if (h->delivery == CORTEX_DELIVERY_DELAY)
+    if (h->delivery == CORTEX_DELIVERY_DELAY) {
+      // the delay-ordered layout reads every piece header: only once the builder has written them
+      // all (a piece over the staging cap or a row over 65,535 records leaves headers unwritten
+      // or truncated)
+      rc = check_err(h, "build");
+      if (rc != CORTEX_OK) return bail(rc);
       TRY(launch_delay_layout(h->nets_d, &h->nets_h[b], h->work_d, b, h->n_warps, h->hdr, h->row_base, h->rec_w,
                               h->rec_meta, h->dtbl, h->dtgt, h->dw, h->err, s),
           "delay-ordered layout");
+    }
   }
   if (h->delivery == CORTEX_DELIVERY_DELAY) {
     TRY(cudaMemsetAsync(h->hist_cnt, 0, 4 * (size_t)h->hist_max * h->n_blocks, s), "memset spike buffer");

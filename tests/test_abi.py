@@ -89,3 +89,43 @@ def test_checkpoint_calls_check_their_arguments_without_gpu():
     assert L.cortex_get_ring(None, 0, buf) == -1
     assert L.cortex_set_state(None, 0, None, None, None, None) == -1
     assert L.cortex_set_step(None, 0) == -1
+
+
+def test_parameter_limits_are_refused_before_any_device_call():
+    """Parameters outside the method's domain (CORTEX_ERR_ARG) or beyond the layout's fields
+    (CORTEX_ERR_UNSUPPORTED: in-degree in a 16-bit draw index, d_max in the 8-bit delay span, the
+    16-bit refractory counter) are refused by the host with a reason, before the device is touched,
+    and leave no handle."""
+    from paper_2406_03762_gb300 import workloads as W
+    L = cortex.load()
+    base = W.NetSpec(800, 200, 80, 20)
+    cases = [
+        (dict(n_exc=0, n_inh=0), cortex.ERR_ARG, "neuron counts"),
+        (dict(k_exc=-1), cortex.ERR_ARG, "in-degree"),
+        (dict(n_inh=0, k_inh=5), cortex.ERR_ARG, "empty population"),
+        (dict(k_exc=60000, k_inh=5536), cortex.ERR_UNSUPPORTED, "in-degree above 65535"),
+        (dict(d_min=0), cortex.ERR_ARG, "d_min"),
+        (dict(d_min=5, d_max=4), cortex.ERR_ARG, "d_min"),
+        (dict(d_max=256), cortex.ERR_UNSUPPORTED, "d_max above 255"),
+        (dict(tau_syn=10.0), cortex.ERR_UNSUPPORTED, "singular propagator"),
+        (dict(dt=0.0), cortex.ERR_ARG, "positive"),
+        (dict(t_ref=3276.8), cortex.ERR_UNSUPPORTED, "refractory counter"),
+        (dict(nu_ext_hz=float("nan")), cortex.ERR_ARG, "nu_ext_hz"),
+        (dict(weight_dtype=7), cortex.ERR_ARG, "weight_dtype"),
+        (dict(e_l=-70.0), cortex.ERR_UNSUPPORTED, "E_L"),
+    ]
+    for change, code, why in cases:
+        p = cortex.params_from_spec(base)
+        for k, v in change.items():
+            setattr(p, k, v)
+        h = ctypes.c_void_p(None)
+        rc = L.cortex_build(ctypes.byref(p), 1, None, None, ctypes.byref(h))
+        assert rc == code, change
+        assert h.value is None, change
+        assert why in L.cortex_last_error().decode(), change
+    # the limits themselves pass the parameter check: the host-only planner accepts them
+    p = cortex.params_from_spec(base)
+    p.k_exc, p.k_inh, p.d_max = 60000, 5535, 255
+    tb, nb = (ctypes.c_int32 * 1)(), ctypes.c_int32(0)
+    assert L.cortex_plan(ctypes.byref(p), 1, None, 152, 232448, tb, ctypes.byref(nb)) == cortex.OK
+    assert nb.value >= 1 and 1 <= tb[0] <= base.n

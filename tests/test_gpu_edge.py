@@ -66,3 +66,29 @@ def test_batch_with_different_delay_ranges(cortex, opts):
         assert np.array_equal(gv.astype(np.float64), ov), f"network {b}"
         total += ref.events
     assert st["events"] == total
+
+
+# Layout limits that only the builder sees, on the device: a source with more than 2,048 synapses
+# into one block (a piece over the staging cap; 10 targets in one block, each drawing 5,000 times
+# from 10 sources) and a source whose row exceeds 65,535 synapses (16-bit piece offsets; 1,000
+# excitatory sources each drawn about 100 times by every one of 100,000 targets).
+OVER_LIMITS = {"piece_over_2048": W.NetSpec(10, 0, 5000, 0),
+               "row_over_65535": W.NetSpec(1000, 99000, 1000, 0)}
+
+
+@pytest.mark.parametrize("name", list(OVER_LIMITS))
+@pytest.mark.parametrize("delivery", [0, 1])
+def test_layout_limits_found_on_the_device_are_refused(cortex, name, delivery):
+    """The build returns CORTEX_ERR_UNSUPPORTED with its reason and leaves no handle (nothing reads
+    the pieces it did not write), and the context stays usable: the next network matches the
+    oracle bit for bit."""
+    with pytest.raises(cortex.CortexError) as e:
+        cortex.Network(OVER_LIMITS[name], 3, cortex.make_options(delivery=delivery))
+    assert e.value.code == cortex.ERR_UNSUPPORTED
+    assert "staging capacity" in str(e.value)
+    spec, seed, steps = EDGE["single_delay"], 5, 300
+    with cortex.Network(spec, seed, cortex.make_options(delivery=delivery)) as net:
+        net.simulate(steps)
+        gs, gi = net.spikes()
+    _, os_, oi, _ = oracle_run(spec, seed, steps)
+    assert len(os_) > 0 and first_mismatch(gs, gi, os_, oi) == -1
