@@ -457,11 +457,17 @@ def _form(cortex, W, name, kw, args, stream, peak, peak_kind, n_steps):
     return out
 
 
+def _deliver_record(config: str, spikes: int) -> str:
+    """profiles/ record of the delivery kernel alone on `spikes` sources of a configuration."""
+    return f"k_step_deliver_{config}_s{spikes}_traffic.json"
+
+
 def _deliver_form(cortex, W, args, stream, peak, peak_kind):
-    """The ring delivery kernel alone (cortex_deliver) on a fixed set of 10,000 spiking sources of
-    the 112,500-neuron network, repeated long enough for the clock samples."""
+    """The ring delivery kernel alone (cortex_deliver, one launch per repetition) on a fixed set of
+    spiking sources (default: 10,000 of the 112,500-neuron network), repeated long enough for the
+    clock samples."""
     import numpy as np
-    cfg = W.CONFIGS["c1"]
+    cfg = W.CONFIGS[args.deliver_config]
     spec = cfg["spec"]
     with cortex.Network(spec, cfg["seed"], cortex.make_options(), stream=stream) as net:
         rng = np.random.default_rng(1)
@@ -477,7 +483,8 @@ def _deliver_form(cortex, W, args, stream, peak, peak_kind):
     return {"workload": cfg["name"], "value": ev / (ms * 1e-3), "unit": UNIT, "spikes_per_launch": int(len(ids)),
             "events_per_launch": ev, "launch_ms": ms, "reps": args.deliver_reps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (delivery phase)"},
+                         "peak_kind": peak_kind, "bytes_per_event": bpe, "kernel": "k_step (delivery phase)",
+                         "traffic": _traffic(ev, _deliver_record(args.deliver_config, len(ids)))},
             "clocks": clk}
 
 
@@ -561,7 +568,9 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="simulate", choices=["simulate", "deliver"])
-    ap.add_argument("--spikes", type=int, default=10000)
+    ap.add_argument("--spikes", type=int, default=10000, help="--mode deliver: spiking sources per launch")
+    ap.add_argument("--deliver-config", default="c1", choices=["c1", "c2", "c3"],
+                    help="--mode deliver: the network whose connectivity is read")
     ap.add_argument("--deliver-reps", type=int, default=300)
     ap.add_argument("--warps", type=int, default=0, help="warps per block (0: library default)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other configurations")
