@@ -38,7 +38,9 @@ def test_traffic_is_reported_only_for_the_measured_kernel():
     """The bench scales a committed record's DRAM bytes per event while the record's digest is the
     current code of the kernel it names, and reports null otherwise (or when there is no record)."""
     found = 0
-    for name in sorted(set(bench.TRAFFIC_RECORDS.values())):
+    deliver = [bench._deliver_record(c, s) for c in ("c1", "c2", "c3") for s in (1000, 10000)]
+    assert bench._deliver_record("c1", 10000) == "k_step_deliver_c1_s10000_traffic.json"
+    for name in sorted(set(bench.TRAFFIC_RECORDS.values()) | set(deliver)):
         path = os.path.join(ROOT, "profiles", name)
         if not os.path.exists(path):
             assert bench._traffic(1e6, name) is None
