@@ -142,3 +142,37 @@ def test_fp32_potentials_track_fp64_within_1e6():
     err, agree = fp64_replay_check(spec, seed, 1000, s32, i32, v32)
     assert agree >= 0.99
     assert err <= 1e-6
+
+
+def test_poisson_drive_stationary_moments_of_current_and_potential():
+    """Unconnected neurons driven by the Poisson input alone, threshold out of reach.  Each step
+    decays I and adds k J_ext with k ~ Poisson(lam), lam = nu_ext dt (I <- P11 I + k J_ext), and V
+    follows V <- P22 V + P21 I with the previous step's I (Eq. 1 and 3, exact integration).
+    Stationary closed forms, with the propagators written out here: E[I] = lam J / (1 - P11),
+    Var[I] = lam J^2 / (1 - P11^2), E[V] = P21 E[I] / (1 - P22).  J_ext differs from the recurrent
+    J_E here, so a drive of the wrong weight shows; so does a drive added before the decay (E[I]
+    scaled by P11, -18%), a drive count that is not Poisson (the variance), or a wrong P21."""
+    n, burn, chunks, every = 2000, 1500, 150, 10
+    nu, h, J = 15000.0, 0.1, 50.0
+    p = o.Params(n_exc=n, n_inh=0, k_exc=0, k_inh=0, v_th=1e9, precision=o.FP64, nu_ext_hz=nu, j_ext=J,
+                 tau_m=TAU_M, tau_syn=TAU_S, c_m=C_M, dt=h)
+    net = o.Network(p, 7)
+    net.set_state(np.zeros(n), np.zeros(n), np.zeros(n, np.int32))  # V0 is drawn below V_th = 1e9
+    net.simulate(burn)
+    cur, pot = [], []
+    for _ in range(chunks):
+        net.simulate(every)
+        v, i, r = net.state()
+        assert not r.any()
+        cur.append(i)
+        pot.append(v)
+    cur, pot = np.concatenate(cur), np.concatenate(pot)
+    lam = nu * h * 1e-3
+    p11, p22 = math.exp(-h / TAU_S), math.exp(-h / TAU_M)
+    p21 = TAU_M * TAU_S / (C_M * (TAU_S - TAU_M)) * (p11 - p22)
+    e_i = lam * J / (1.0 - p11)
+    var_i = lam * J * J / (1.0 - p11 * p11)
+    e_v = p21 * e_i / (1.0 - p22)
+    assert abs(cur.mean() / e_i - 1.0) < 0.01
+    assert abs(cur.var() / var_i - 1.0) < 0.03
+    assert abs(pot.mean() / e_v - 1.0) < 0.01
