@@ -176,3 +176,48 @@ def test_poisson_drive_stationary_moments_of_current_and_potential():
     assert abs(cur.mean() / e_i - 1.0) < 0.01
     assert abs(cur.var() / var_i - 1.0) < 0.03
     assert abs(pot.mean() / e_v - 1.0) < 0.01
+
+
+def _siegert_rate_hz(nu_hz, s):
+    """Output rate of an LIF neuron with exponential synaptic currents driven by Poisson inputs in
+    the diffusion approximation (Siegert's first-passage formula; Brunel, J. Comput. Neurosci. 8,
+    2000), with the threshold and reset shifted by (alpha / 2) sqrt(tau_s / tau_m), alpha =
+    sqrt(2) |zeta(1/2)|, for the synaptic filtering (Fourcaud and Brunel, Neural Comput. 14, 2002).
+    Every input neuron fires at nu_hz; the external drive is Poisson at nu_ext."""
+    from scipy import integrate, special
+    tm, ts, c = s.tau_m, s.tau_syn, s.c_m
+    nu, ne = nu_hz * 1e-3, s.nu_ext_hz * 1e-3  # per ms
+    # charge J tau_s per input spike: mean and variance of the free membrane potential
+    mu = tm / c * ts * (s.k_exc * nu * s.j_exc + s.k_inh * nu * s.j_inh + ne * s.j_ext)
+    var = tm / (c * c) * ts * ts * (s.k_exc * nu * s.j_exc ** 2 + s.k_inh * nu * s.j_inh ** 2 + ne * s.j_ext ** 2) / 2
+    sig = math.sqrt(var)
+    shift = math.sqrt(2.0) * abs(special.zeta(0.5)) / 2 * math.sqrt(ts / tm)
+    lo, hi = (s.v_reset - mu) / sig + shift, (s.v_th - mu) / sig + shift
+    # e^{u^2} (1 + erf u) = erfcx(-u)
+    integral, _ = integrate.quad(lambda u: special.erfcx(-u), lo, hi, limit=200)
+    return 1e3 / (s.t_ref + tm * math.sqrt(math.pi) * integral)
+
+
+def test_mean_driven_balanced_network_rate_matches_mean_field():
+    """The 2,500-neuron balanced network (K = 250, g = 5, 15 kHz drive) sits in the mean-driven
+    regime (free mean potential about 22.6 mV above the 20 mV threshold), where the diffusion
+    approximation holds: the oracle's population rates after the first 100 ms agree with the
+    self-consistent mean-field rate (about 43 Hz) within 10%, and the two populations, which have
+    the same in-degrees, fire alike.  Dropping or halving the inhibition, or a drive of the wrong
+    weight, moves the rate far outside that band."""
+    from scipy import optimize
+    from helpers import oracle_params
+    from paper_2406_03762_gb300 import workloads as W
+    cfg = W.CONFIGS["c0"]
+    spec = cfg["spec"]
+    nu_mf = optimize.brentq(lambda x: x - _siegert_rate_hz(x, spec), 0.1, 500.0)
+    net = o.Network(oracle_params(spec, o.FP32), cfg["seed"])
+    steps, skip = 4000, 1000
+    net.simulate(steps)
+    st, ids = net.raster()
+    late = st >= skip
+    secs = (steps - skip) * spec.dt * 1e-3
+    rate_e = np.sum(late & (ids < spec.n_exc)) / spec.n_exc / secs
+    rate_i = np.sum(late & (ids >= spec.n_exc)) / spec.n_inh / secs
+    assert abs(rate_e / nu_mf - 1.0) < 0.10 and abs(rate_i / nu_mf - 1.0) < 0.10, (rate_e, rate_i, nu_mf)
+    assert abs(rate_e / rate_i - 1.0) < 0.03
